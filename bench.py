@@ -1,0 +1,455 @@
+"""Benchmark of the GB300 bitmap sort.
+
+Default workload: one array of n = 2^24 distinct uint32 keys drawn uniformly
+without replacement from [0, 2^28) (Floyd sampling + shuffle), max_value =
+2^28 - 1 (32 MiB bitmap).  One step = one sort of the whole array (every step
+of the path: range check, scatter, popcount, scan, emission) through the C
+ABI call `bitsort_ex`, inputs already resident in HBM.  L2 is flushed between
+timed steps (a 512 MiB write, outside the timed events).
+
+Other workloads (--workload): c0 (n=1e5, M=2^20), c2a (n=2^31, M=2^32),
+c2b (n=2^24, M=2^32), batched (4096 arrays, one launch, graph replay),
+served (Poisson arrivals through the serving loop).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank sorts its own array (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sorted Gkeys/s and % HBM roofline, plain vs batched/served; p50/p99 latency"
+SEED = 0x13120138
+
+WORKLOADS = {
+    "c0": dict(n=100_000, M=1 << 20, method="floyd", cfg=0,
+               desc="plain bitsort, one array: n=100000 distinct uint32 from [0,2^20), max_value=2^20-1"),
+    "c1": dict(n=1 << 24, M=1 << 28, method="floyd", cfg=1,
+               desc="plain bitsort, one array: n=2^24 distinct uint32 from [0,2^28) (density 1/16), "
+                    "max_value=2^28-1, bitmap 32 MiB"),
+    "c2a": dict(n=1 << 31, M=1 << 32, method="feistel", cfg=2,
+                desc="plain bitsort, dense full range: n=2^31 distinct uint32 from [0,2^32) (Feistel "
+                     "permutation stand-in for sampling without replacement)"),
+    "c2b": dict(n=1 << 24, M=1 << 32, method="feistel", cfg=2,
+                desc="plain bitsort, sparse full range: n=2^24 distinct uint32 from [0,2^32) (density 1/256)"),
+}
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def engine_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1312_0138_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1312_0138_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summary, only if it was
+    taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("source_hash") == engine_source_hash():
+            return e.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, value):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_keys(w, rank):
+    import gen
+    return gen.keys(SEED + w["cfg"] + 1000 * rank, w["n"], w["M"], w["method"])
+
+
+# ------------------------------------------------------------ CPU oracle
+def time_oracle(keys_np, max_value, budget_s=10.0, max_keys=None):
+    """Oracle on the host (single thread) on a bounded sample: whole runs of
+    the array (or of its first max_keys keys) until budget_s has elapsed."""
+    import oracle
+    sample = keys_np if max_keys is None or keys_np.size <= max_keys else keys_np[:max_keys]
+    runs, t_total = 0, 0.0
+    while t_total < budget_s or runs == 0:
+        t0 = time.perf_counter()
+        st, out = oracle.bitmap_sort(sample, max_value)
+        t_total += time.perf_counter() - t0
+        runs += 1
+        if runs >= 50:
+            break
+    return {"value": runs * sample.size / t_total / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": f"{runs} single-threaded oracle run(s) over {sample.size} keys of the workload "
+                      f"(max_value={max_value}), {t_total:.1f} s"}
+
+
+def run_reference(args, w, ws, rank):
+    if rank != 0:
+        return
+    keys_np = make_keys(w, rank)
+    M = w["M"]
+    per_step = []
+    max_keys = 1 << 24 if w["n"] > (1 << 24) else None
+    for _ in range(args.warmup + args.steps):
+        r = time_oracle(keys_np, M - 1, budget_s=0.0, max_keys=max_keys)
+        per_step.append(r)
+    vals = [r["value"] for r in per_step[args.warmup:]]
+    v = float(np.median(vals))
+    n_step = min(w["n"], max_keys or w["n"])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gkeys/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": n_step / (v * 1e9) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": w["desc"], "n": w["n"], "max_value": M - 1},
+            "cpu_baseline": {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step one single-threaded oracle run over {n_step} keys"},
+            "e2e": {"value": v, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+def run_plain(args, w, ws, rank, local):
+    import torch
+    import paper_1312_0138_gb300 as bs
+
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    bs.load()
+    ctx = bs.Context(dev)
+    keys_np = make_keys(w, rank)
+    n, M = w["n"], w["M"]
+    keys = torch.from_numpy(keys_np.view(np.int32)).cuda()
+    out = torch.empty_like(keys)
+    if args.tune:
+        ctx.autotune(keys, M - 1, out=out)
+    if args.path:
+        ctx.set_config(n, M - 1, {"fused": 1, "partition": 2, "global": 3}[args.path], args.slice, args.threads)
+    cfg = ctx.get_config(n, M - 1)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # correctness of the measured configuration (one sort, checked on device)
+    st, cnt, _ = ctx.sort(keys, M - 1, out=out)
+    assert st == bs.OK and cnt == n, (st, cnt)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        ctx.sort_async(keys, M - 1, out=out)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = ctx.kernel_launches()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)                      # evict keys/out/bitmap from L2
+        starts[i].record(stream)
+        ctx.sort_async(keys, M - 1, out=out)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = ctx.kernel_launches() - launches0
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_step = float(np.mean(ms))
+    ms_step_max = max_over_ranks(ws, ms_step)
+    st, cnt = ctx.sync_status()
+    assert st == bs.OK and cnt == n
+
+    value = ws * n / (ms_step_max * 1e-3) / 1e9
+    peak, peak_kind = read_peaks()
+    algo_bytes = 8 * n + M // 4
+    achieved = algo_bytes / (ms_step * 1e-3) / 1e9
+
+    # end to end: pinned host keys -> device, sort, device -> pinned host out
+    e2e_steps = max(3, min(args.steps, args.e2e_steps))
+    hkeys = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
+    hout = torch.empty(n, dtype=torch.int32).pin_memory()
+    hres = torch.zeros(2, dtype=torch.int64).pin_memory()
+    dres = torch.zeros(2, dtype=torch.int64, device="cuda")
+    dk = torch.empty_like(keys)
+    do = torch.empty_like(keys)
+    for _ in range(2):
+        dk.copy_(hkeys, non_blocking=True)
+        ctx.sort_async(dk, M - 1, out=do, result=dres)
+        hout.copy_(do, non_blocking=True)
+        hres.copy_(dres, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        dk.copy_(hkeys, non_blocking=True)
+        ctx.sort_async(dk, M - 1, out=do, result=dres)
+        hout.copy_(do, non_blocking=True)
+        hres.copy_(dres, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1) / e2e_steps)
+    assert int(hres[0]) & 0xFFFFFFFF == bs.OK and int(hres[1]) == n
+    assert bool(np.all(np.diff(hout.numpy().view(np.uint32)[:1 << 20].astype(np.int64)) > 0))
+
+    if rank != 0:
+        return
+    cpu = time_oracle(keys_np, M - 1, budget_s=args.cpu_budget,
+                      max_keys=1 << 24 if n > (1 << 24) else None) if not args.no_cpu else None
+    traffic = recorded_traffic(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w["desc"], "n": n, "max_value": M - 1, "keys": w["method"],
+                   "l2": "flushed between timed steps (512 MiB write, outside the step events)",
+                   "path": cfg["path"], "slice_values": cfg["slice_values"], "threads": cfg["threads"],
+                   "wall_s": wall},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "note": f"algorithmic bytes 8n+M/4 = {algo_bytes} per launch (keys in, bitmap "
+                             f"write+read, keys out) / mean event time of the one engine launch per step; "
+                             f"peak = {peak_kind} copy bandwidth"},
+        "e2e": {"value": ws * n / (e2e_ms * 1e-3) / 1e9, "unit": "Gkeys/s", "h2d_bytes_per_step": 4 * n,
+                "d2h_bytes_per_step": 4 * n + 16},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args, ws, rank, local):
+    """configs[3]: 4096 arrays in one persistent launch (graph replay) vs the
+    same arrays as 4096 plain launches."""
+    import torch
+    import gen
+    import paper_1312_0138_gb300 as bs
+
+    torch.cuda.set_device(local)
+    ctx = bs.Context(local)
+    spec = gen.batch_spec(SEED + 3 + 1000 * rank, args.batch_count)
+    keys, outs, arrays = [], [], []
+    total = 0
+    for i, (n, M) in enumerate(spec):
+        k = torch.from_numpy(gen.feistel(SEED + 7 * i + 1000 * rank, n, M).view(np.int32)).cuda()
+        o = torch.empty_like(k)
+        keys.append(k)
+        outs.append(o)
+        arrays.append((k, M - 1, o))
+        total += n
+    plan = ctx.plan(arrays)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        plan.launch()
+    res = plan.results()
+    assert all(st == bs.OK for st, _ in res)
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    batched_ms = float(np.median(ms))
+    # the same arrays as independent plain launches
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(3)
+    e0.record(stream)
+    for k, mv, o in arrays:
+        ctx.sort_async(k, mv, out=o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    peak, _ = read_peaks()
+    algo = sum(8 * n + M // 4 for n, M in spec)
+    line = {"metric": METRIC, "value": total / (batched_ms * 1e-3) / 1e9, "unit": "Gkeys/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batched bitsort, {len(spec)} arrays in one persistent launch (CUDA graph), "
+                                   f"n log-uniform [2^10,2^22], max_value log-uniform [2^12,2^26], density [1/64,1/2]",
+                       "total_keys": total, "plain_launches_ms": plain_ms,
+                       "plain_launches_gkeys_s": total / (plain_ms * 1e-3) / 1e9,
+                       "speedup_vs_plain_launches": plain_ms / batched_ms},
+            "roofline": {"bound": "hbm", "achieved": algo / (batched_ms * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": algo / (batched_ms * 1e-3) / 1e9 / peak, "traffic": None}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_served(args, ws, rank, local):
+    """configs[4]: Poisson arrivals through the serving loop."""
+    import torch
+    import gen
+    import paper_1312_0138_gb300 as bs
+
+    torch.cuda.set_device(local)
+    count = args.serve_count
+    spec = gen.serve_spec(SEED + 4, count, rate_hz=args.rate)
+    reqs = []
+    for i, (t, n, M) in enumerate(spec):
+        k = torch.from_numpy(gen.feistel(SEED + 11 * i, n, M).view(np.int32)).cuda()
+        reqs.append((t, k, M - 1, torch.empty_like(k)))
+    srv = bs.Server(local, budget_bytes=40 << 30, max_inflight=args.inflight)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = []
+    for t, k, mv, o in reqs:
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        tickets.append(srv.submit(k, mv, o))
+    lats = []
+    for tk in tickets:
+        st, cnt, lat = srv.wait(tk)
+        assert st == bs.OK
+        lats.append(lat)
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    total = sum(n for _, n, _ in spec)
+    line = {"metric": METRIC, "value": total / wall / 1e9, "unit": "Gkeys/s", "n_gpus": ws, "steps": count,
+            "warmup": 0, "ms_per_step": wall * 1e3 / count, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"served bitsort, {count} Poisson requests at {args.rate}/s, n log-uniform "
+                                   f"[2^10,2^26], max_value log-uniform [2^16,2^32-1], 40 GiB budget",
+                       "p50_ms": float(np.percentile(lats, 50)) * 1e3,
+                       "p99_ms": float(np.percentile(lats, 99)) * 1e3, "batches": stats["batches"],
+                       "max_concurrent_batches": stats["max_concurrent"], "total_keys": total}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c1", choices=list(WORKLOADS) + ["batched", "served"])
+    ap.add_argument("--path", default=None, choices=[None, "fused", "partition", "global"])
+    ap.add_argument("--slice", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--serve-count", type=int, default=400)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--inflight", type=int, default=4)
+    args = ap.parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        w = WORKLOADS.get(args.workload, WORKLOADS["c1"])
+        run_reference(args, w, ws, rank)
+        return
+    if args.workload == "batched":
+        run_batched(args, ws, rank, local)
+    elif args.workload == "served":
+        run_served(args, ws, rank, local)
+    else:
+        run_plain(args, WORKLOADS[args.workload], ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * bitsort.h -- C ABI of the GB300 (sm_103a) bitmap sort.
+ *
+ * The operation is the paper's bitwise sort of an integer array (K. Yordzhev,
+ * "The bitwise operations related to a fast sorting algorithm", Section V,
+ * Algorithm 1; Theorem 1: the result is the array in ascending order;
+ * Theorem 2: linear time).  It is computed here in its bit-set form: key x
+ * sets bit (x mod 32) of word floor(x / 32) of a bitmap with OR and a shifted
+ * one (Table I; Example 2); the words are then read in index order and the
+ * positions of the set bits, bit 0 first inside a word (bit numbering of
+ * Section II), are written out.  That form needs two things the paper's own
+ * listing does not: the keys must be DISTINCT (one bit cannot count
+ * repetitions) and BOUNDED by `max_value` (the bitmap has max_value + 1
+ * bits).  Under those two conditions the output equals the paper's result.
+ *
+ * Conventions for every call below:
+ *   - keys/out are DEVICE pointers to uint32_t arrays of n elements unless a
+ *     call says otherwise.  out == keys (sorting in place, as the paper's
+ *     function does) is allowed; any other overlap of the two ranges is
+ *     BITSORT_ERR_INVALID.
+ *   - M = max_value + 1 is computed in 64 bits (max_value may be 2^32 - 1).
+ *   - Calls are asynchronous with respect to the host: they enqueue work on
+ *     `stream` and return.  Host-checkable errors (null pointer with n > 0,
+ *     n > M, partial overlap, allocation failure) are returned at once and
+ *     nothing is enqueued.  Data-dependent outcomes are written on the device
+ *     into a bitsort_result_t and are read after the stream completes.
+ *   - Data-dependent outcomes:
+ *       BITSORT_OK            out[0..n) = keys in ascending order.
+ *       BITSORT_ERR_KEY_RANGE some key > max_value: such keys are skipped;
+ *                             out[0..count) = the distinct in-range keys in
+ *                             ascending order, out[count..n) unspecified.
+ *       BITSORT_ERR_DUPLICATE a key occurs more than once: out[0..count) =
+ *                             the distinct keys ascending (count < n),
+ *                             out[count..n) unspecified.  KEY_RANGE takes
+ *                             precedence when both hold.
+ *       BITSORT_ERR_TIMEOUT   a bounded device-side wait ran out (a stalled
+ *                             predecessor); out is unspecified.  The context
+ *                             resets its scratch when it reports this.
+ *   - A context (bitsort_ctx_t) owns the device scratch of the calls made
+ *     with it.  Calls that share a context must be ordered on the device
+ *     (same stream, or ordered by events); concurrent calls on different
+ *     streams need different contexts.
+ */
+#ifndef BITSORT_H_
+#define BITSORT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without including the CUDA headers (same underlying type). */
+typedef struct CUstream_st *bitsort_stream_t;
+
+typedef enum {
+    BITSORT_OK = 0,
+    BITSORT_ERR_INVALID = 1,   /* bad argument (host check) */
+    BITSORT_ERR_KEY_RANGE = 2, /* a key above max_value (device) */
+    BITSORT_ERR_DUPLICATE = 3, /* repeated keys (device) */
+    BITSORT_ERR_NOMEM = 4,     /* device or host allocation failed */
+    BITSORT_ERR_TIMEOUT = 5,   /* a bounded device wait expired */
+    BITSORT_ERR_CUDA = 6,      /* a CUDA runtime call failed */
+    BITSORT_ERR_BUDGET = 7     /* a served request can never fit the budget */
+} bitsort_status_t;
+
+/* Device-written outcome of one sort: status is a bitsort_status_t value,
+ * count the number of values written to out. 16 bytes, 8-byte aligned. */
+typedef struct {
+    uint32_t status;
+    uint32_t reserved;
+    uint64_t count;
+} bitsort_result_t;
+
+typedef struct bitsort_ctx bitsort_ctx_t;
+
+/* ----------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (made current by the call).
+ * Returns BITSORT_ERR_INVALID for a bad device, BITSORT_ERR_NOMEM on failure
+ * to allocate its fixed scratch. *ctx receives the handle. */
+bitsort_status_t bitsort_ctx_create(int device, bitsort_ctx_t **ctx);
+
+/* Synchronise the device and free everything the context owns. */
+bitsort_status_t bitsort_ctx_destroy(bitsort_ctx_t *ctx);
+
+/* Text for a status code (static storage). */
+const char *bitsort_status_string(bitsort_status_t status);
+
+/* ------------------------------------------------------------- single sort */
+
+/* Sort n distinct uint32 keys bounded by max_value (Algorithm 1's problem,
+ * bitmap form).  Uses a per-device default context created on first use.
+ * The data-dependent result is kept in that context; read it with
+ * bitsort_sync_status(NULL, stream, &count). */
+bitsort_status_t bitsort(const uint32_t *keys, size_t n, uint32_t max_value, uint32_t *out,
+                         bitsort_stream_t stream);
+
+/* As bitsort(), with an explicit context (NULL = the current device's default
+ * context) and an optional DEVICE pointer `d_result` that receives the
+ * outcome (NULL = keep it in the context). */
+bitsort_status_t bitsort_ex(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n, uint32_t max_value,
+                            uint32_t *out, bitsort_result_t *d_result, bitsort_stream_t stream);
+
+/* Wait for `stream`, then return the status of the last sort that wrote its
+ * outcome into the context (and its count through `count`, nullable). */
+bitsort_status_t bitsort_sync_status(bitsort_ctx_t *ctx, bitsort_stream_t stream, uint64_t *count);
+
+/* ---------------------------------------------------------------- batching */
+
+/* One array of a batch.  keys/out are device pointers; the same rules as
+ * bitsort() apply to each array independently. */
+typedef struct {
+    const uint32_t *keys;
+    uint32_t *out;
+    uint64_t n;
+    uint32_t max_value;
+    uint32_t reserved;
+} bitsort_desc_t;
+
+typedef struct bitsort_batch_plan bitsort_batch_plan_t;
+
+/* Sort `count` independent arrays in one persistent launch.  `descs` is a
+ * HOST array; `d_results` a DEVICE array of `count` outcomes (nullable).
+ * Builds a plan, launches it once and frees the plan (stream-ordered). */
+bitsort_status_t bitsort_batched(bitsort_ctx_t *ctx, const bitsort_desc_t *descs, size_t count,
+                                 bitsort_result_t *d_results, bitsort_stream_t stream);
+
+/* Build a reusable plan for a batch: the per-array strategy (fused shared
+ * memory slice, partition + shared-memory slices, or global L2 bitmap), the
+ * work list, and the device scratch.  The plan owns its scratch and a device
+ * array of `count` outcomes.  The pointers in descs are baked in. */
+bitsort_status_t bitsort_batch_plan_create(bitsort_ctx_t *ctx, const bitsort_desc_t *descs, size_t count,
+                                           bitsort_batch_plan_t **plan);
+
+/* Enqueue the plan on `stream`.  The first launch on a stream captures the
+ * launch sequence into a CUDA graph; later launches replay it.  Launches of
+ * one plan must be ordered on the device. */
+bitsort_status_t bitsort_batch_plan_launch(bitsort_batch_plan_t *plan, bitsort_stream_t stream);
+
+/* Copy the plan's outcomes to HOST memory `results` (count entries) after
+ * synchronising `stream`.  Returns the first non-OK status, or OK. */
+bitsort_status_t bitsort_batch_plan_results(bitsort_batch_plan_t *plan, bitsort_stream_t stream,
+                                            bitsort_result_t *results);
+
+/* Device pointer to the plan's outcome array (count entries). */
+const bitsort_result_t *bitsort_batch_plan_device_results(const bitsort_batch_plan_t *plan);
+
+bitsort_status_t bitsort_batch_plan_destroy(bitsort_batch_plan_t *plan);
+
+/* ----------------------------------------------------------------- serving */
+
+typedef struct bitsort_server bitsort_server_t;
+
+/* A continuous-batching sort server on `device`.  Requests are admitted in
+ * arrival order while the bytes their bitmap and output need
+ * (ceil(M/8) + 4n, M = max_value + 1) fit in `budget_bytes`; admitted
+ * requests are batched as they arrive and launched on up to
+ * `max_inflight` concurrent streams, so that their device work overlaps. */
+bitsort_status_t bitsort_server_create(int device, uint64_t budget_bytes, int max_inflight,
+                                       bitsort_server_t **server);
+
+/* Queue one request (device pointers, caller-owned until it completes).
+ * Returns BITSORT_ERR_BUDGET if the request alone exceeds the budget,
+ * BITSORT_ERR_INVALID for bad arguments.  *ticket identifies it. */
+bitsort_status_t bitsort_server_submit(bitsort_server_t *server, const uint32_t *keys, uint64_t n,
+                                       uint32_t max_value, uint32_t *out, uint64_t *ticket);
+
+/* Block until request `ticket` has completed; its outcome, count and latency
+ * (completion minus submission, seconds) are returned (pointers nullable). */
+bitsort_status_t bitsort_server_wait(bitsort_server_t *server, uint64_t ticket, bitsort_status_t *status,
+                                     uint64_t *count, double *latency_s);
+
+/* Counters since creation: completed requests, keys sorted, launched batches,
+ * and the largest number of batches seen in flight at once (nullable). */
+bitsort_status_t bitsort_server_stats(bitsort_server_t *server, uint64_t *completed, uint64_t *keys,
+                                      uint64_t *batches, uint64_t *max_concurrent);
+
+/* Drain outstanding requests, stop the scheduler and free the server. */
+bitsort_status_t bitsort_server_destroy(bitsort_server_t *server);
+
+/* -------------------------------------------------------------- autotuning */
+
+/* Strategies a plan may use for one array. */
+typedef enum {
+    BITSORT_PATH_AUTO = 0,
+    BITSORT_PATH_FUSED = 1,     /* one CTA, bitmap in shared memory (M <= slice) */
+    BITSORT_PATH_PARTITION = 2, /* high-bit partition, one shared-memory slice per bucket */
+    BITSORT_PATH_GLOBAL = 3     /* atomicOr into a global (L2-resident) bitmap, then scan */
+} bitsort_path_t;
+
+/* Time the candidate configurations (path x slice size x block size) on
+ * representative DEVICE data: n distinct keys bounded by max_value in `keys`
+ * (left unchanged) and a separate DEVICE buffer `out` of n elements (keys and
+ * out must not overlap).  Each candidate runs once to warm up, then five
+ * times with L2 flushed in between; the one with the smallest median time
+ * goes into the context's table for the size class (ceil(log2 n),
+ * ceil(log2 M)) and is reported (pointers nullable).  Synchronises. */
+bitsort_status_t bitsort_autotune(bitsort_ctx_t *ctx, const uint32_t *keys, uint32_t *out, uint64_t n,
+                                  uint32_t max_value, bitsort_path_t *path, uint32_t *slice_values,
+                                  uint32_t *block_threads, double *best_ms);
+
+/* Force a configuration for the size class of (n, max_value) (testing and
+ * benchmarking): path, values per shared-memory slice (a multiple of 32; 0 =
+ * default) and threads per block (256 or 512; 0 = default). */
+bitsort_status_t bitsort_set_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max_value, bitsort_path_t path,
+                                    uint32_t slice_values, uint32_t block_threads);
+
+/* The configuration the context would use for (n, max_value). */
+bitsort_status_t bitsort_get_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max_value, bitsort_path_t *path,
+                                    uint32_t *slice_values, uint32_t *block_threads);
+
+/* Save / load the tuned table as JSON text at `path`. */
+bitsort_status_t bitsort_tune_save(bitsort_ctx_t *ctx, const char *path);
+bitsort_status_t bitsort_tune_load(bitsort_ctx_t *ctx, const char *path);
+
+/* ------------------------------------------------------------- diagnostics */
+
+/* Upper bound of every bounded device-side wait, in milliseconds (default
+ * 4000).  A wait that runs out reports BITSORT_ERR_TIMEOUT instead of
+ * hanging the GPU. */
+bitsort_status_t bitsort_set_wait_limit_ms(bitsort_ctx_t *ctx, uint32_t ms);
+
+/* Launch a partition-path sort of keys/n/max_value whose bucket stage waits
+ * for one partition tile that is never scheduled: every bounded wait must
+ * run out and the outcome must be BITSORT_ERR_TIMEOUT.  For testing the
+ * failure path; the context stays usable afterwards. */
+bitsort_status_t bitsort_debug_stalled_launch(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n,
+                                              uint32_t max_value, uint32_t *out, bitsort_stream_t stream);
+
+/* Number of kernels the library enqueued since the context was created. */
+uint64_t bitsort_kernel_launches(const bitsort_ctx_t *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BITSORT_H_ */

@@ -1,0 +1,356 @@
+"""GB300 (sm_103a) bitmap sort: Python binding of the C ABI in include/bitsort.h.
+
+The operation is the paper's bitwise sort of an integer array (Section V,
+Algorithm 1; Theorem 1 fixes the result: the keys in ascending order), done in
+its bit-set form on the GPU: every key sets one bit of a bitmap (Table I OR of
+a shifted one, Example 2), the set bits are counted (Example 6) and their
+positions written out in order (Section II bit numbering).  Keys are distinct
+uint32 values bounded by ``max_value``.
+
+This module only marshals arguments: tensors are passed to the CUDA library by
+device pointer together with the current torch stream; every step of the sort
+runs in the library's kernels.  If ``libbitsort.so`` is missing or cannot be
+loaded, importing a function raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Iterable, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbitsort.so")
+
+OK, ERR_INVALID, ERR_KEY_RANGE, ERR_DUPLICATE, ERR_NOMEM, ERR_TIMEOUT, ERR_CUDA, ERR_BUDGET = range(8)
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "KEY_RANGE", 3: "DUPLICATE", 4: "NOMEM", 5: "TIMEOUT",
+                6: "CUDA", 7: "BUDGET"}
+PATH_AUTO, PATH_FUSED, PATH_PARTITION, PATH_GLOBAL = range(4)
+PATH_NAMES = {0: "auto", 1: "fused", 2: "partition", 3: "global"}
+
+# names every build must export (checked by the CPU test-suite)
+EXPORTS = [
+    "bitsort_ctx_create", "bitsort_ctx_destroy", "bitsort_status_string", "bitsort", "bitsort_ex",
+    "bitsort_sync_status", "bitsort_batched", "bitsort_batch_plan_create", "bitsort_batch_plan_launch",
+    "bitsort_batch_plan_results", "bitsort_batch_plan_device_results", "bitsort_batch_plan_destroy",
+    "bitsort_server_create", "bitsort_server_submit", "bitsort_server_wait", "bitsort_server_stats",
+    "bitsort_server_destroy", "bitsort_autotune", "bitsort_set_config", "bitsort_get_config",
+    "bitsort_tune_save", "bitsort_tune_load", "bitsort_set_wait_limit_ms", "bitsort_debug_stalled_launch",
+    "bitsort_kernel_launches",
+]
+
+
+class BitsortError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}" if what else STATUS_NAMES.get(status, str(status)))
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("count", ctypes.c_uint64)]
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("max_value", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import builder as _b
+    return _b.build(force=force)
+
+
+def _declare(lib):
+    p, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    st = ctypes.c_int
+    sig = {
+        "bitsort_ctx_create": (st, [i32, ctypes.POINTER(p)]),
+        "bitsort_ctx_destroy": (st, [p]),
+        "bitsort_status_string": (ctypes.c_char_p, [i32]),
+        "bitsort": (st, [p, ctypes.c_size_t, u32, p, p]),
+        "bitsort_ex": (st, [p, p, u64, u32, p, p, p]),
+        "bitsort_sync_status": (st, [p, p, ctypes.POINTER(u64)]),
+        "bitsort_batched": (st, [p, p, ctypes.c_size_t, p, p]),
+        "bitsort_batch_plan_create": (st, [p, p, ctypes.c_size_t, ctypes.POINTER(p)]),
+        "bitsort_batch_plan_launch": (st, [p, p]),
+        "bitsort_batch_plan_results": (st, [p, p, p]),
+        "bitsort_batch_plan_device_results": (p, [p]),
+        "bitsort_batch_plan_destroy": (st, [p]),
+        "bitsort_server_create": (st, [i32, u64, i32, ctypes.POINTER(p)]),
+        "bitsort_server_submit": (st, [p, p, u64, u32, p, ctypes.POINTER(u64)]),
+        "bitsort_server_wait": (st, [p, u64, ctypes.POINTER(i32), ctypes.POINTER(u64),
+                                     ctypes.POINTER(ctypes.c_double)]),
+        "bitsort_server_stats": (st, [p] + [ctypes.POINTER(u64)] * 4),
+        "bitsort_server_destroy": (st, [p]),
+        "bitsort_autotune": (st, [p, p, p, u64, u32, ctypes.POINTER(i32), ctypes.POINTER(u32),
+                                  ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_double)]),
+        "bitsort_set_config": (st, [p, u64, u32, i32, u32, u32]),
+        "bitsort_get_config": (st, [p, u64, u32, ctypes.POINTER(i32), ctypes.POINTER(u32),
+                                    ctypes.POINTER(u32)]),
+        "bitsort_tune_save": (st, [p, ctypes.c_char_p]),
+        "bitsort_tune_load": (st, [p, ctypes.c_char_p]),
+        "bitsort_set_wait_limit_ms": (st, [p, u32]),
+        "bitsort_debug_stalled_launch": (st, [p, p, u64, u32, p, p]),
+        "bitsort_kernel_launches": (u64, [p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def load(path: Optional[str] = None):
+    """Load libbitsort.so (raises if it was not built: no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = path or LIB_PATH
+            if not os.path.exists(path):
+                raise ImportError(f"libbitsort.so not built ({path}); run __graft_entry__.build()")
+            _lib = _declare(ctypes.CDLL(path))
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise BitsortError(status, what)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if t.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("keys/out must be int32 or uint32 tensors (uint32 values)")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+class Context:
+    """A bitsort context on one device: scratch, tuned table, launch counter."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.bitsort_ctx_create(device, ctypes.byref(h)), "bitsort_ctx_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            load().bitsort_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # single sort -----------------------------------------------------------
+    def sort_async(self, keys, max_value: int, out=None, result=None, stream=None):
+        """Enqueue the sort of `keys` (device tensor) into `out`; returns out.
+
+        `result` is an optional device tensor of 2 int64 (bitsort_result_t)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(keys)
+        rptr = result.data_ptr() if result is not None else None
+        st = load().bitsort_ex(self.handle, _ptr(keys) if keys.numel() else None, keys.numel(),
+                               int(max_value), _ptr(out) if out.numel() else None, rptr, _stream_handle(stream))
+        _check(st, "bitsort_ex")
+        return out
+
+    def sync_status(self, stream=None):
+        cnt = ctypes.c_uint64(0)
+        st = load().bitsort_sync_status(self.handle, _stream_handle(stream), ctypes.byref(cnt))
+        return st, cnt.value
+
+    def sort(self, keys, max_value: int, out=None, stream=None):
+        """Sort and wait: returns (status, count, out)."""
+        out = self.sort_async(keys, max_value, out=out, stream=stream)
+        st, cnt = self.sync_status(stream)
+        return st, cnt, out
+
+    # tuning ----------------------------------------------------------------
+    def set_config(self, n: int, max_value: int, path: int, slice_values: int = 0, threads: int = 0):
+        _check(load().bitsort_set_config(self.handle, n, max_value, path, slice_values, threads),
+               "bitsort_set_config")
+
+    def get_config(self, n: int, max_value: int):
+        p, s, t = ctypes.c_int(0), ctypes.c_uint32(0), ctypes.c_uint32(0)
+        _check(load().bitsort_get_config(self.handle, n, max_value, ctypes.byref(p), ctypes.byref(s),
+                                         ctypes.byref(t)), "bitsort_get_config")
+        return {"path": PATH_NAMES[p.value], "slice_values": s.value, "threads": t.value}
+
+    def autotune(self, keys, max_value: int, out=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(keys)
+        p, s, t, ms = ctypes.c_int(0), ctypes.c_uint32(0), ctypes.c_uint32(0), ctypes.c_double(0)
+        _check(load().bitsort_autotune(self.handle, _ptr(keys), _ptr(out), keys.numel(), int(max_value),
+                                       ctypes.byref(p), ctypes.byref(s), ctypes.byref(t), ctypes.byref(ms)),
+               "bitsort_autotune")
+        return {"path": PATH_NAMES[p.value], "slice_values": s.value, "threads": t.value, "ms": ms.value}
+
+    def tune_save(self, path: str):
+        _check(load().bitsort_tune_save(self.handle, path.encode()), "bitsort_tune_save")
+
+    def tune_load(self, path: str):
+        _check(load().bitsort_tune_load(self.handle, path.encode()), "bitsort_tune_load")
+
+    def set_wait_limit_ms(self, ms: int):
+        _check(load().bitsort_set_wait_limit_ms(self.handle, ms), "bitsort_set_wait_limit_ms")
+
+    def debug_stalled_launch(self, keys, max_value: int, out, stream=None):
+        _check(load().bitsort_debug_stalled_launch(self.handle, _ptr(keys), keys.numel(), int(max_value),
+                                                   _ptr(out), _stream_handle(stream)), "debug_stalled_launch")
+
+    def kernel_launches(self) -> int:
+        return int(load().bitsort_kernel_launches(self.handle))
+
+    # batching --------------------------------------------------------------
+    def batched(self, arrays: Sequence, results=None, stream=None):
+        """Sort [(keys, max_value, out), ...] in one launch; `results` is an
+        optional device tensor of len(arrays) x 2 int64 outcomes."""
+        descs = _descs(arrays)
+        rptr = results.data_ptr() if results is not None else None
+        _check(load().bitsort_batched(self.handle, ctypes.byref(descs), len(arrays), rptr,
+                                      _stream_handle(stream)), "bitsort_batched")
+
+    def plan(self, arrays: Sequence) -> "BatchPlan":
+        return BatchPlan(self, arrays)
+
+
+def _descs(arrays):
+    descs = (Desc * len(arrays))()
+    for i, (keys, max_value, out) in enumerate(arrays):
+        descs[i].keys = _ptr(keys) if keys.numel() else None
+        descs[i].out = _ptr(out) if out.numel() else None
+        descs[i].n = keys.numel()
+        descs[i].max_value = int(max_value)
+    return descs
+
+
+class BatchPlan:
+    """A reusable batched sort (one persistent launch, replayed from a CUDA graph)."""
+
+    def __init__(self, ctx: Context, arrays: Sequence):
+        self.ctx = ctx
+        self.count = len(arrays)
+        self._keep = list(arrays)
+        h = ctypes.c_void_p()
+        descs = _descs(arrays)
+        _check(load().bitsort_batch_plan_create(ctx.handle, ctypes.byref(descs), self.count, ctypes.byref(h)),
+               "bitsort_batch_plan_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(load().bitsort_batch_plan_launch(self.handle, _stream_handle(stream)), "bitsort_batch_plan_launch")
+
+    def results(self, stream=None):
+        res = (Result * self.count)()
+        load().bitsort_batch_plan_results(self.handle, _stream_handle(stream), ctypes.byref(res))
+        return [(r.status, r.count) for r in res]
+
+    def close(self):
+        if self.handle:
+            load().bitsort_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching sort server (admission by a device-memory budget)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 40 << 30, max_inflight: int = 4):
+        h = ctypes.c_void_p()
+        _check(load().bitsort_server_create(device, budget_bytes, max_inflight, ctypes.byref(h)),
+               "bitsort_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, keys, max_value: int, out) -> int:
+        t = ctypes.c_uint64(0)
+        _check(load().bitsort_server_submit(self.handle, _ptr(keys) if keys.numel() else None, keys.numel(),
+                                            int(max_value), _ptr(out) if out.numel() else None, ctypes.byref(t)),
+               "bitsort_server_submit")
+        self._keep[t.value] = (keys, out)
+        return t.value
+
+    def wait(self, ticket: int):
+        st, cnt, lat = ctypes.c_int(0), ctypes.c_uint64(0), ctypes.c_double(0)
+        load().bitsort_server_wait(self.handle, ticket, ctypes.byref(st), ctypes.byref(cnt), ctypes.byref(lat))
+        self._keep.pop(ticket, None)
+        return st.value, cnt.value, lat.value
+
+    def stats(self):
+        v = [ctypes.c_uint64(0) for _ in range(4)]
+        load().bitsort_server_stats(self.handle, *[ctypes.byref(x) for x in v])
+        return {"completed": v[0].value, "keys": v[1].value, "batches": v[2].value,
+                "max_concurrent": v[3].value}
+
+    def close(self):
+        if self.handle:
+            load().bitsort_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = {}
+
+
+def default_context(device: Optional[int] = None) -> Context:
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    if dev not in _default_ctx:
+        _default_ctx[dev] = Context(dev)
+    return _default_ctx[dev]
+
+
+def bitsort(keys, max_value: int, out=None, stream=None):
+    """The plain call: enqueue the sort of `keys` into `out` on `stream`
+    (default: torch's current stream) through the C entry point `bitsort`
+    (per-device default context); returns `out`.  Host-checkable errors raise
+    BitsortError; read the data-dependent status with :func:`sync_status`."""
+    import torch
+    if out is None:
+        out = torch.empty_like(keys)
+    st = load().bitsort(_ptr(keys) if keys.numel() else None, keys.numel(), int(max_value),
+                        _ptr(out) if out.numel() else None, _stream_handle(stream))
+    _check(st, "bitsort")
+    return out
+
+
+def sync_status(stream=None):
+    """Status and count of the last plain `bitsort` call (waits for `stream`)."""
+    cnt = ctypes.c_uint64(0)
+    st = load().bitsort_sync_status(None, _stream_handle(stream), ctypes.byref(cnt))
+    return st, cnt.value

@@ -1,0 +1,611 @@
+// api.cu -- host side of the C ABI in include/bitsort.h: contexts, planning,
+// launching, batching with CUDA graphs, autotuning.
+//
+// Planning an array (n keys, M = max_value + 1 possible values) means picking
+//   FUSED      one BUCKET item reads the whole array into one shared-memory
+//              bitmap (needs M <= the largest slice);
+//   PARTITION  HIST + PART tiles move the keys to contiguous bucket ranges
+//              (bucket = value range of S values, S a multiple of 32), then
+//              one BUCKET item per bucket;
+//   GLOBAL     GSCATTER tiles OR the keys into a global bitmap in L2, then
+//              one GSCAN item per slice of S values;
+// together with the slice size S and the block size.  The choice comes from
+// the context's tuned table (bitsort_autotune / bitsort_tune_load) or, for a
+// size class never tuned, from a fixed rule.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "internal.h"
+
+using namespace bsx;
+
+namespace {
+
+constexpr uint32_t kMaxSliceValues = 1u << 20;   // 128 KiB of bitmap per CTA
+constexpr uint64_t kDefaultWaitNs = 4000ull * 1000ull * 1000ull;
+
+inline uint32_t round_up_u32(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
+inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+inline int ilog2_ceil(uint64_t v) {
+    int k = 0;
+    while (k < 64 && (1ull << k) < v) ++k;
+    return k;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- context
+bitsort_status_t bsx_check(cudaError_t e) {
+    if (e == cudaSuccess) return BITSORT_OK;
+    if (e == cudaErrorMemoryAllocation) return BITSORT_ERR_NOMEM;
+    return BITSORT_ERR_CUDA;
+}
+
+static bitsort_status_t ctx_alloc_fixed(bitsort_ctx *c) {
+    // small block: ticket[4] | sync[8] | result(16 B), then per-slice arrays
+    size_t small = 256;
+    size_t per = (size_t)kMaxSlices;
+    size_t bytes = small + per * (4 + 4 + 8 + 8);
+    cudaError_t e = cudaMalloc(&c->fixed, bytes);
+    if (e != cudaSuccess) return bsx_check(e);
+    e = cudaMemset(c->fixed, 0, bytes);
+    if (e != cudaSuccess) return bsx_check(e);
+    char *p = (char *)c->fixed;
+    c->ticket = (uint32_t *)p;
+    c->sync = (uint32_t *)(p + 16);
+    c->result = (bitsort_result_t *)(p + 64);
+    c->counts = (uint32_t *)(p + small);
+    c->cursor = c->counts + per;
+    c->offsets = (uint64_t *)(c->cursor + per);
+    c->look = c->offsets + per;
+    c->fixed_bytes = bytes;
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_ctx_create(int device, bitsort_ctx_t **out) {
+    if (!out) return BITSORT_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return BITSORT_ERR_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) return BITSORT_ERR_CUDA;
+    bitsort_ctx *c = new (std::nothrow) bitsort_ctx();
+    if (!c) return BITSORT_ERR_NOMEM;
+    c->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return BITSORT_ERR_CUDA;
+    }
+    c->sms = prop.multiProcessorCount;
+    c->l2_bytes = (size_t)prop.l2CacheSize;
+    // dynamic shared memory available next to the kernel's static block
+    c->smem_optin = (uint32_t)prop.sharedMemPerBlockOptin - 1024;
+    c->wait_limit_ns = kDefaultWaitNs;
+    if (engine_set_smem_limit(256, c->smem_optin) != 0 || engine_set_smem_limit(512, c->smem_optin) != 0) {
+        delete c;
+        return BITSORT_ERR_CUDA;
+    }
+    bitsort_status_t st = ctx_alloc_fixed(c);
+    if (st != BITSORT_OK) {
+        if (c->fixed) cudaFree(c->fixed);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_ctx_destroy(bitsort_ctx_t *c) {
+    if (!c) return BITSORT_ERR_INVALID;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->fixed) cudaFree(c->fixed);
+    if (c->part) cudaFree(c->part);
+    if (c->bitmap) cudaFree(c->bitmap);
+    if (c->flush) cudaFree(c->flush);
+    delete c;
+    return BITSORT_OK;
+}
+
+extern "C" const char *bitsort_status_string(bitsort_status_t s) {
+    switch (s) {
+        case BITSORT_OK: return "ok";
+        case BITSORT_ERR_INVALID: return "invalid argument";
+        case BITSORT_ERR_KEY_RANGE: return "key above max_value";
+        case BITSORT_ERR_DUPLICATE: return "duplicate keys";
+        case BITSORT_ERR_NOMEM: return "out of memory";
+        case BITSORT_ERR_TIMEOUT: return "device wait timed out";
+        case BITSORT_ERR_CUDA: return "CUDA error";
+        case BITSORT_ERR_BUDGET: return "request exceeds the memory budget";
+    }
+    return "unknown status";
+}
+
+static std::mutex g_default_mu;
+static std::map<int, bitsort_ctx *> g_default;
+
+bitsort_ctx *bsx_default_ctx() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_default_mu);
+    auto it = g_default.find(dev);
+    if (it != g_default.end()) return it->second;
+    bitsort_ctx *c = nullptr;
+    if (bitsort_ctx_create(dev, &c) != BITSORT_OK) return nullptr;
+    g_default[dev] = c;
+    return c;
+}
+
+// ------------------------------------------------------------- planning
+uint64_t bsx_div_magic(uint32_t S) {
+    // ceil(2^64 / S); exact floor(x / S) = mulhi(x, magic) for all x < 2^32
+    // when S < 2^32 (the error x * (magic - 2^64/S) / 2^64 < 1/S).
+    return UINT64_MAX / S + 1;
+}
+
+bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M) {
+    bsx_config cfg;
+    cfg.threads = 512;
+    if (M <= (1ull << 17) || (M <= kMaxSliceValues && n <= (1ull << 16))) {
+        cfg.path = BITSORT_PATH_FUSED;
+        cfg.S = round_up_u32((uint32_t)M, 128);
+        return cfg;
+    }
+    cfg.path = BITSORT_PATH_PARTITION;
+    uint64_t target = 2ull * (uint64_t)c->sms;
+    uint64_t S = ceil_div(M, target);
+    uint64_t lo = std::max<uint64_t>(4096, ceil_div(M, kMaxSlices));
+    S = std::max(S, lo);
+    S = std::min<uint64_t>(S, kMaxSliceValues);
+    cfg.S = round_up_u32((uint32_t)S, 128);
+    return cfg;
+}
+
+bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->table.find(std::make_pair(ilog2_ceil(n), ilog2_ceil(M)));
+    if (it != c->table.end()) return it->second;
+    return bsx_default_config(c, n, M);
+}
+
+// Make a configuration valid for (n, M): the slice count within bounds, the
+// slice a multiple of 128 values, FUSED only where one slice covers M.
+bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
+    if (cfg.threads != 256 && cfg.threads != 512) cfg.threads = 512;
+    if (cfg.path == BITSORT_PATH_FUSED && M > kMaxSliceValues) cfg.path = BITSORT_PATH_PARTITION;
+    if (cfg.path == BITSORT_PATH_FUSED) {
+        cfg.S = round_up_u32((uint32_t)M, 128);
+        return cfg;
+    }
+    if (cfg.path != BITSORT_PATH_PARTITION && cfg.path != BITSORT_PATH_GLOBAL) cfg.path = BITSORT_PATH_PARTITION;
+    uint64_t S = cfg.S ? cfg.S : (1u << 18);
+    S = std::max<uint64_t>(S, ceil_div(M, kMaxSlices));
+    S = std::min<uint64_t>(S, kMaxSliceValues);
+    S = std::max<uint64_t>(S, 128);
+    cfg.S = round_up_u32((uint32_t)S, 128);
+    (void)n;
+    return cfg;
+}
+
+uint32_t bsx_smem_for(const bsx_config &cfg, uint32_t nslices, uint32_t tile_keys) {
+    uint32_t s = slice_smem_bytes(cfg.S, cfg.threads);
+    if (cfg.path == BITSORT_PATH_PARTITION) {
+        s = std::max(s, part_smem_bytes(nslices, tile_keys));
+        s = std::max(s, hist_smem_bytes(nslices));
+    }
+    return s;
+}
+
+// Fill the descriptor of one array and append its item segments.
+void bsx_describe(const bsx_config &cfg, const uint32_t *keys, uint32_t *out, uint64_t n, uint64_t M,
+                  ArrayDesc &a) {
+    memset(&a, 0, sizeof(a));
+    a.keys = keys;
+    a.out = out;
+    a.n = n;
+    a.M = M;
+    a.path = (uint32_t)cfg.path;
+    a.S = cfg.S;
+    a.div_magic = bsx_div_magic(cfg.S);
+    a.nslices = (uint32_t)ceil_div(M, cfg.S);
+    a.tile_keys = (uint32_t)(kKeysPerThread * cfg.threads);
+    a.key_tiles = (uint32_t)ceil_div(n, a.tile_keys);
+    if (cfg.path == BITSORT_PATH_FUSED) {
+        a.nslices = 1;
+        a.key_tiles = 0;
+    }
+}
+
+bool bsx_ranges_overlap(const void *a, const void *b, uint64_t bytes) {
+    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+static bitsort_status_t ensure_part(bitsort_ctx *c, uint64_t n) {
+    if (c->part_cap >= n) return BITSORT_OK;
+    if (c->part) {
+        cudaDeviceSynchronize();
+        cudaFree(c->part);
+        c->part = nullptr;
+        c->part_cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->part, n * sizeof(uint32_t));
+    if (e != cudaSuccess) return bsx_check(e);
+    c->part_cap = n;
+    return BITSORT_OK;
+}
+
+static bitsort_status_t ensure_bitmap(bitsort_ctx *c, uint64_t M) {
+    const uint64_t words = (ceil_div(M, 32) + 3) / 4 * 4;
+    if (c->bitmap_words >= words) return BITSORT_OK;
+    if (c->bitmap) {
+        cudaDeviceSynchronize();
+        cudaFree(c->bitmap);
+        c->bitmap = nullptr;
+        c->bitmap_words = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->bitmap, words * 4);
+    if (e != cudaSuccess) return bsx_check(e);
+    e = cudaMemset(c->bitmap, 0, words * 4);
+    if (e != cudaSuccess) return bsx_check(e);
+    c->bitmap_words = words;
+    return BITSORT_OK;
+}
+
+int bsx_grid_for(bitsort_ctx *c, int threads, uint32_t smem, uint32_t items) {
+    int per_sm = 1;
+    if (engine_max_blocks_per_sm(threads, smem, &per_sm) != 0 || per_sm < 1) per_sm = 1;
+    uint64_t g = (uint64_t)per_sm * (uint64_t)c->sms;
+    if (g > items) g = items;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// Segments of a single array, ticket order: HIST, PART, BUCKET or
+// GSCATTER, GSCAN or one BUCKET (fused).
+uint32_t bsx_single_segments(const ArrayDesc &a, Segment *seg, uint32_t *nseg) {
+    uint32_t t = 0, k = 0;
+    auto add = [&](uint32_t type, uint32_t count) {
+        if (count == 0) return;
+        seg[k].start = t;
+        seg[k].array = 0;
+        seg[k].type = type;
+        seg[k].first = 0;
+        ++k;
+        t += count;
+    };
+    if (a.path == BITSORT_PATH_FUSED) {
+        add(IT_BUCKET, 1);
+    } else if (a.path == BITSORT_PATH_PARTITION) {
+        add(IT_HIST, a.key_tiles);
+        add(IT_PART, a.key_tiles);
+        add(IT_BUCKET, a.nslices);
+    } else {
+        add(IT_GSCATTER, a.key_tiles);
+        add(IT_GSCAN, a.nslices);
+    }
+    *nseg = k;
+    return t;
+}
+
+static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, const uint32_t *keys, uint64_t n,
+                                      uint64_t M, uint32_t *out, bitsort_result_t *d_result, cudaStream_t stream,
+                                      uint32_t stall) {
+    bsx_config cfg = bsx_sanitize(cfg0, n, M);
+    EngineParams p;
+    memset(&p, 0, sizeof(p));
+    ArrayDesc &a = p.one;
+    bsx_describe(cfg, keys, out, n, M, a);
+    a.stall = stall;
+    bool alias = keys == out;
+    if (cfg.path == BITSORT_PATH_PARTITION) {
+        if (alias) {
+            bitsort_status_t st = ensure_part(c, n);
+            if (st != BITSORT_OK) return st;
+            a.part = c->part;
+        } else {
+            a.part = out;  // partition in the output buffer, sort in place per bucket
+        }
+    }
+    if (cfg.path == BITSORT_PATH_GLOBAL) {
+        bitsort_status_t st = ensure_bitmap(c, M);
+        if (st != BITSORT_OK) return st;
+        a.bitmap = c->bitmap;
+    }
+    a.counts = c->counts;
+    a.cursor = c->cursor;
+    a.offsets = c->offsets;
+    a.look = c->look;
+    a.sync = c->sync;
+    a.result = d_result ? d_result : c->result;
+    p.arrays = nullptr;
+    p.segments = nullptr;
+    p.total_items = bsx_single_segments(a, p.seg, &p.nseg);
+    p.ticket = c->ticket;
+    p.wait_limit_ns = c->wait_limit_ns;
+    uint32_t smem = bsx_smem_for(cfg, a.nslices, a.tile_keys);
+    if (smem > c->smem_optin) return BITSORT_ERR_INVALID;
+    int grid = bsx_grid_for(c, cfg.threads, smem, p.total_items);
+    int e = engine_launch(p, cfg.threads, smem, grid, stream);
+    if (e != 0) return BITSORT_ERR_CUDA;
+    c->launches.fetch_add(1);
+    return BITSORT_OK;
+}
+
+static bitsort_status_t write_trivial_result(bitsort_ctx *c, bitsort_result_t *d_result, cudaStream_t s) {
+    bitsort_result_t *r = d_result ? d_result : c->result;
+    return bsx_check(cudaMemsetAsync(r, 0, sizeof(bitsort_result_t), s));
+}
+
+bitsort_status_t bsx_validate(const uint32_t *keys, uint64_t n, uint32_t max_value, const uint32_t *out) {
+    if (n == 0) return BITSORT_OK;
+    if (!keys || !out) return BITSORT_ERR_INVALID;
+    uint64_t M = (uint64_t)max_value + 1;
+    if (n > M) return BITSORT_ERR_INVALID;  // pigeonhole: keys cannot be distinct
+    if (((uintptr_t)keys & 3u) || ((uintptr_t)out & 3u)) return BITSORT_ERR_INVALID;
+    if (keys != out && bsx_ranges_overlap(keys, out, n * sizeof(uint32_t))) return BITSORT_ERR_INVALID;
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_ex(bitsort_ctx_t *c, const uint32_t *keys, uint64_t n, uint32_t max_value,
+                                       uint32_t *out, bitsort_result_t *d_result, bitsort_stream_t stream) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    bitsort_status_t st = bsx_validate(keys, n, max_value, out);
+    if (st != BITSORT_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;
+    if (n == 0) return write_trivial_result(c, d_result, s);
+    uint64_t M = (uint64_t)max_value + 1;
+    bsx_config cfg = bsx_lookup_config(c, n, M);
+    return launch_single(c, cfg, keys, n, M, out, d_result, s, 0);
+}
+
+extern "C" bitsort_status_t bitsort(const uint32_t *keys, size_t n, uint32_t max_value, uint32_t *out,
+                                    bitsort_stream_t stream) {
+    return bitsort_ex(nullptr, keys, (uint64_t)n, max_value, out, nullptr, stream);
+}
+
+bitsort_status_t bsx_reset_scratch(bitsort_ctx *c) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return BITSORT_ERR_CUDA;
+    e = cudaMemset(c->fixed, 0, c->fixed_bytes);
+    if (e == cudaSuccess && c->bitmap) e = cudaMemset(c->bitmap, 0, c->bitmap_words * 4);
+    return bsx_check(e);
+}
+
+extern "C" bitsort_status_t bitsort_sync_status(bitsort_ctx_t *c, bitsort_stream_t stream, uint64_t *count) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BITSORT_ERR_CUDA;
+    bitsort_result_t r;
+    if (cudaMemcpy(&r, c->result, sizeof(r), cudaMemcpyDeviceToHost) != cudaSuccess) return BITSORT_ERR_CUDA;
+    if (count) *count = r.count;
+    if (r.status == BITSORT_ERR_TIMEOUT) bsx_reset_scratch(c);
+    return (bitsort_status_t)r.status;
+}
+
+extern "C" bitsort_status_t bitsort_set_wait_limit_ms(bitsort_ctx_t *c, uint32_t ms) {
+    if (!c) c = bsx_default_ctx();
+    if (!c || ms == 0) return BITSORT_ERR_INVALID;
+    c->wait_limit_ns = (uint64_t)ms * 1000000ull;
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_debug_stalled_launch(bitsort_ctx_t *c, const uint32_t *keys, uint64_t n,
+                                                         uint32_t max_value, uint32_t *out,
+                                                         bitsort_stream_t stream) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    bitsort_status_t st = bsx_validate(keys, n, max_value, out);
+    if (st != BITSORT_OK || n == 0) return st == BITSORT_OK ? BITSORT_ERR_INVALID : st;
+    uint64_t M = (uint64_t)max_value + 1;
+    bsx_config cfg;
+    cfg.path = BITSORT_PATH_PARTITION;
+    cfg.threads = 256;
+    cfg.S = (uint32_t)std::max<uint64_t>(128, ceil_div(M, 4));  // four buckets
+    return launch_single(c, cfg, keys, n, M, out, nullptr, reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+extern "C" uint64_t bitsort_kernel_launches(const bitsort_ctx_t *c) {
+    if (!c) return 0;
+    return c->launches.load();
+}
+
+// --------------------------------------------------------------- tuning
+extern "C" bitsort_status_t bitsort_set_config(bitsort_ctx_t *c, uint64_t n, uint32_t max_value, bitsort_path_t path,
+                                               uint32_t slice_values, uint32_t block_threads) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    uint64_t M = (uint64_t)max_value + 1;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto key = std::make_pair(ilog2_ceil(n), ilog2_ceil(M));
+    if (path == BITSORT_PATH_AUTO) {
+        c->table.erase(key);
+        return BITSORT_OK;
+    }
+    bsx_config cfg = bsx_default_config(c, n, M);
+    cfg.path = path;
+    if (slice_values) cfg.S = slice_values;
+    if (block_threads) cfg.threads = (int)block_threads;
+    c->table[key] = bsx_sanitize(cfg, n, M);
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_get_config(bitsort_ctx_t *c, uint64_t n, uint32_t max_value, bitsort_path_t *path,
+                                               uint32_t *slice_values, uint32_t *block_threads) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    uint64_t M = (uint64_t)max_value + 1;
+    bsx_config cfg = bsx_sanitize(bsx_lookup_config(c, n, M), n, M);
+    if (path) *path = cfg.path;
+    if (slice_values) *slice_values = cfg.S;
+    if (block_threads) *block_threads = (uint32_t)cfg.threads;
+    return BITSORT_OK;
+}
+
+// Candidate configurations for (n, M), deduplicated after sanitizing.
+std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_t M) {
+    std::vector<bsx_config> out;
+    auto push = [&](bitsort_path_t path, uint64_t S, int threads) {
+        bsx_config cfg;
+        cfg.path = path;
+        cfg.S = (uint32_t)std::min<uint64_t>(S, 0xFFFFFF80u);
+        cfg.threads = threads;
+        cfg = bsx_sanitize(cfg, n, M);
+        for (auto &o : out)
+            if (o.path == cfg.path && o.S == cfg.S && o.threads == cfg.threads) return;
+        out.push_back(cfg);
+    };
+    for (int threads : {256, 512}) {
+        if (M <= kMaxSliceValues) push(BITSORT_PATH_FUSED, M, threads);
+        for (int k : {1, 2, 3, 4, 6, 8}) push(BITSORT_PATH_PARTITION, ceil_div(M, (uint64_t)k * c->sms), threads);
+        for (int lg : {16, 17, 18, 19, 20}) push(BITSORT_PATH_PARTITION, 1ull << lg, threads);
+        for (int lg : {14, 16, 18, 20}) push(BITSORT_PATH_GLOBAL, 1ull << lg, threads);
+    }
+    // shared memory must fit
+    std::vector<bsx_config> fit;
+    for (auto &cfg : out) {
+        ArrayDesc a;
+        bsx_describe(cfg, nullptr, nullptr, n, M, a);
+        if (bsx_smem_for(cfg, a.nslices, a.tile_keys) <= c->smem_optin) fit.push_back(cfg);
+    }
+    return fit;
+}
+
+static bitsort_status_t ensure_flush(bitsort_ctx *c) {
+    if (c->flush) return BITSORT_OK;
+    size_t bytes = std::max<size_t>(2 * c->l2_bytes, 256u << 20);
+    cudaError_t e = cudaMalloc(&c->flush, bytes);
+    if (e != cudaSuccess) return bsx_check(e);
+    c->flush_bytes = bytes;
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_autotune(bitsort_ctx_t *c, const uint32_t *keys, uint32_t *out, uint64_t n,
+                                             uint32_t max_value, bitsort_path_t *path, uint32_t *slice_values,
+                                             uint32_t *block_threads, double *best_ms) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    bitsort_status_t st = bsx_validate(keys, n, max_value, out);
+    if (st != BITSORT_OK) return st;
+    if (n == 0 || keys == out) return BITSORT_ERR_INVALID;
+    if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;
+    uint64_t M = (uint64_t)max_value + 1;
+    if ((st = ensure_flush(c)) != BITSORT_OK) return st;
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return BITSORT_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    bsx_config best_cfg = bsx_default_config(c, n, M);
+    for (const bsx_config &cfg : bsx_candidates(c, n, M)) {
+        // one warm-up, then the median of five cold-L2 runs
+        if (launch_single(c, cfg, keys, n, M, out, nullptr, s, 0) != BITSORT_OK) continue;
+        std::vector<float> ts;
+        bool ok = true;
+        for (int r = 0; r < 5 && ok; ++r) {
+            cudaMemsetAsync(c->flush, r, c->flush_bytes, s);
+            cudaEventRecord(e0, s);
+            ok = launch_single(c, cfg, keys, n, M, out, nullptr, s, 0) == BITSORT_OK;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ts.push_back(ms);
+        }
+        bitsort_result_t r;
+        cudaMemcpy(&r, c->result, sizeof(r), cudaMemcpyDeviceToHost);
+        if (!ok || r.status != BITSORT_OK) {
+            if (r.status == BITSORT_ERR_TIMEOUT) bsx_reset_scratch(c);
+            continue;
+        }
+        std::sort(ts.begin(), ts.end());
+        double med = ts[ts.size() / 2];
+        if (med < best) {
+            best = med;
+            best_cfg = cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (best >= 1e30) return BITSORT_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        best_cfg.ms = best;
+        c->table[std::make_pair(ilog2_ceil(n), ilog2_ceil(M))] = best_cfg;
+    }
+    if (path) *path = best_cfg.path;
+    if (slice_values) *slice_values = best_cfg.S;
+    if (block_threads) *block_threads = (uint32_t)best_cfg.threads;
+    if (best_ms) *best_ms = best;
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_tune_save(bitsort_ctx_t *c, const char *path) {
+    if (!c) c = bsx_default_ctx();
+    if (!c || !path) return BITSORT_ERR_INVALID;
+    FILE *f = fopen(path, "w");
+    if (!f) return BITSORT_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    fprintf(f, "{\"version\": 1, \"entries\": [");
+    bool first = true;
+    for (auto &kv : c->table) {
+        fprintf(f, "%s\n  {\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, \"ms\": %.6f}",
+                first ? "" : ",", kv.first.first, kv.first.second, (int)kv.second.path, kv.second.S,
+                kv.second.threads, kv.second.ms);
+        first = false;
+    }
+    fprintf(f, "\n]}\n");
+    fclose(f);
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path) {
+    if (!c) c = bsx_default_ctx();
+    if (!c || !path) return BITSORT_ERR_INVALID;
+    FILE *f = fopen(path, "r");
+    if (!f) return BITSORT_ERR_INVALID;
+    std::string text;
+    char buf[4096];
+    size_t k;
+    while ((k = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, k);
+    fclose(f);
+    std::map<std::pair<int, int>, bsx_config> table;
+    size_t pos = 0;
+    while ((pos = text.find("{\"log2n\"", pos)) != std::string::npos) {
+        int ln = 0, lm = 0, p = 0, th = 0;
+        unsigned S = 0;
+        double ms = 0;
+        if (sscanf(text.c_str() + pos,
+                   "{\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, \"ms\": %lf",
+                   &ln, &lm, &p, &S, &th, &ms) != 6)
+            return BITSORT_ERR_INVALID;
+        if (p < 1 || p > 3 || (th != 256 && th != 512) || ln < 0 || ln > 64 || lm < 0 || lm > 33)
+            return BITSORT_ERR_INVALID;
+        bsx_config cfg;
+        cfg.path = (bitsort_path_t)p;
+        cfg.S = S;
+        cfg.threads = th;
+        cfg.ms = ms;
+        table[std::make_pair(ln, lm)] = cfg;
+        ++pos;
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (auto &kv : table) c->table[kv.first] = kv.second;
+    return BITSORT_OK;
+}

@@ -1,0 +1,605 @@
+// engine.cu -- the persistent sort kernel for sm_103a.
+//
+// One kernel runs every step of the bitmap form of the paper's bitwise sort
+// (Section V, Algorithm 1; result fixed by Theorem 1) for one or many arrays.
+// Work items are taken from a ticket counter in ascending order; see engine.h
+// for the item types.  Design points:
+//   * keys stream through 128-bit loads with the streaming cache hint; the
+//     head and tail of a range that is not 16-byte aligned are peeled;
+//   * the bitmap of a bucket lives in shared memory, where the OR of a
+//     shifted one (Table I, Example 2) is a native shared-memory atomic;
+//   * the per-word popcount (Example 6) of a slice is summed per warp, and the
+//     number of set bits before the slice comes from a decoupled look-back
+//     (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled
+//     Look-back", NVIDIA NVR-2016-002) over the slices of the array;
+//   * set-bit positions are written ascending, bit 0 first inside a word
+//     (Section II numbering), staged per warp in shared memory so that every
+//     global store of a warp covers consecutive elements;
+//   * every wait on another CTA is bounded in time (%globaltimer) and in
+//     iterations, and reports a timeout instead of hanging.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "engine.h"
+
+namespace bsx {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t bucket_of(uint32_t x, uint64_t magic) {
+    return (uint32_t)__umul64hi((uint64_t)x, magic);
+}
+
+__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += y;
+    }
+    return v;
+}
+__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t y = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += y;
+    }
+    return v;
+}
+
+struct SharedMisc {
+    uint64_t wsum[33];
+    uint64_t excl;
+    uint32_t wcount[32];
+    uint32_t wbase[32];
+    uint32_t ticket;
+    uint32_t flag;
+    uint32_t total;
+};
+
+// Thread 0 only: wait until *p >= target.  Gives up (false) when the array's
+// timeout flag is raised by another CTA, after `limit_ns` of wall time, or
+// after an iteration cap that bounds the loop even if the timer misbehaves.
+__device__ bool wait_geq(const uint32_t *p, uint32_t target, const uint32_t *timeout_flag, uint64_t limit_ns) {
+    if (ld_acquire_u32(p) >= target) return true;
+    const uint64_t t0 = now_ns();
+    const uint64_t cap = limit_ns / 16 + 4096;
+    uint32_t sleep = 32;
+    for (uint64_t it = 0; it < cap; ++it) {
+        __nanosleep(sleep);
+        if (sleep < 2048) sleep <<= 1;
+        if (ld_acquire_u32(p) >= target) return true;
+        if ((it & 7) == 7) {
+            if (ld_acquire_u32(timeout_flag) != 0) return false;
+            if (now_ns() - t0 > limit_ns) return false;
+        }
+    }
+    return false;
+}
+
+// Exclusive prefix sums of load(0..nb) passed to store(i, prefix); returns
+// the total.  Every thread of the block must call it.
+template <int T, class Load, class Store>
+__device__ uint64_t block_exclusive_scan(uint32_t nb, Load load, Store store, SharedMisc &m) {
+    constexpr int NW = T / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (nb + T - 1) / T;
+    const uint32_t lo = min(nb, threadIdx.x * per), hi = min(nb, lo + per);
+    uint64_t s = 0;
+    for (uint32_t i = lo; i < hi; ++i) s += load(i);
+    const uint64_t incl = warp_incl_scan_u64(s, lane);
+    if (lane == 31) m.wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t w = lane < NW ? m.wsum[lane] : 0;
+        const uint64_t wi = warp_incl_scan_u64(w, lane);
+        if (lane < NW) m.wsum[lane] = wi - w;
+        if (lane == 31) m.wsum[32] = wi;
+    }
+    __syncthreads();
+    uint64_t run = m.wsum[warp] + incl - s;
+    for (uint32_t i = lo; i < hi; ++i) {
+        const uint64_t c = load(i);
+        store(i, run);
+        run += c;
+    }
+    const uint64_t total = m.wsum[32];
+    __syncthreads();
+    return total;
+}
+
+// Calls f(key) for every key of p[lo, hi): 128-bit streaming loads for the
+// 16-byte aligned body, scalar loads for the peeled head and tail.
+template <int T, bool kStream, class F>
+__device__ __forceinline__ void for_each_key(const uint32_t *p, uint64_t lo, uint64_t hi, F &&f) {
+    if (lo >= hi) return;
+    const uint32_t mis = (uint32_t)((reinterpret_cast<uintptr_t>(p + lo) & 15u) >> 2);
+    uint64_t head = mis ? 4u - mis : 0u;
+    if (head > hi - lo) head = hi - lo;
+    if (threadIdx.x < head) f(kStream ? __ldcs(p + lo + threadIdx.x) : __ldcg(p + lo + threadIdx.x));
+    const uint64_t b0 = lo + head;
+    const uint64_t nv = (hi - b0) >> 2;
+    const uint4 *v = reinterpret_cast<const uint4 *>(p + b0);
+    uint64_t i = threadIdx.x;
+    for (; i + 7 * (uint64_t)T < nv; i += 8 * (uint64_t)T) {
+        uint4 q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = kStream ? __ldcs(v + i + u * T) : __ldcg(v + i + u * T);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            f(q[u].x);
+            f(q[u].y);
+            f(q[u].z);
+            f(q[u].w);
+        }
+    }
+    for (; i < nv; i += T) {
+        const uint4 q = kStream ? __ldcs(v + i) : __ldcg(v + i);
+        f(q.x);
+        f(q.y);
+        f(q.z);
+        f(q.w);
+    }
+    const uint64_t t0 = b0 + (nv << 2);
+    if (t0 + threadIdx.x < hi) f(kStream ? __ldcs(p + t0 + threadIdx.x) : __ldcg(p + t0 + threadIdx.x));
+}
+
+// ------------------------------------------------------------- look-back
+// Warp 0 of the CTA that owns slice s: publish the slice's own count, add up
+// the counts of the slices before it (stopping at the nearest published
+// inclusive prefix), publish the inclusive prefix and return the exclusive
+// one.  Bounded: on timeout the array's timeout flag is raised and 0 is used.
+__device__ uint64_t lookback(const EngineParams &P, const ArrayDesc &a, uint32_t s, uint32_t agg, int lane) {
+    uint64_t *look = a.look;
+    if (s == 0) {
+        if (lane == 0) st_release_u64(&look[0], LB_PREFIX | agg);
+        return 0;
+    }
+    if (lane == 0) st_release_u64(&look[s], LB_AGG | agg);
+    uint64_t excl = 0;
+    int64_t j = (int64_t)s - 1;
+    bool expired = false;
+    uint64_t t0 = 0;
+    uint64_t iters = 0;
+    const uint64_t cap = P.wait_limit_ns / 16 + 4096;
+    while (true) {
+        const int64_t idx = j - lane;
+        uint64_t v = idx >= 0 ? ld_acquire_u64(&look[idx]) : LB_PREFIX;
+        while (__any_sync(kFull, (v >> 62) == 0)) {
+            if (iters == 0) t0 = now_ns();
+            ++iters;
+            if ((iters & 7) == 0) {
+                bool stop = false;
+                if (lane == 0)
+                    stop = iters > cap || now_ns() - t0 > P.wait_limit_ns ||
+                           ld_acquire_u32(&a.sync[SY_TIMEOUT]) != 0;
+                if (__shfl_sync(kFull, stop ? 1 : 0, 0)) {
+                    expired = true;
+                    break;
+                }
+            }
+            __nanosleep(64);
+            if ((v >> 62) == 0) v = ld_acquire_u64(&look[idx]);
+        }
+        if (expired) break;
+        const unsigned pmask = __ballot_sync(kFull, (v >> 62) == 2);
+        uint64_t val = v & LB_VALUE;
+        if (pmask) {
+            const int first = __ffs(pmask) - 1;  // nearest slice with a prefix
+            if (lane > first) val = 0;
+            excl += warp_sum_u64(val);
+            break;
+        }
+        excl += warp_sum_u64(val);
+        j -= 32;
+    }
+    if (expired) {
+        if (lane == 0) atomicOr(&a.sync[SY_TIMEOUT], 1u);
+        excl = 0;
+    }
+    if (lane == 0) st_release_u64(&look[s], LB_PREFIX | (excl + agg));
+    return excl;
+}
+
+// Count, look back and write out one bitmap slice held in shared memory.
+// `bm` holds `words` words covering the values v0 .. v0 + 32*words - 1.
+template <int T>
+__device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t s, const uint32_t *bm,
+                             uint32_t words, uint32_t v0, uint32_t *stage_all, SharedMisc &m) {
+    constexpr int NW = T / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t wpw = ((((words + NW - 1) / NW) + 31u) & ~31u);
+    const uint32_t w0 = min(words, (uint32_t)warp * wpw), w1 = min(words, w0 + wpw);
+
+    uint32_t cnt = 0;
+    for (uint32_t i = w0 + lane; i < w1; i += 32) cnt += __popc(bm[i]);
+    cnt = warp_sum_u32(cnt);
+    if (lane == 0) m.wcount[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t c = lane < NW ? m.wcount[lane] : 0;
+        const uint32_t incl = warp_incl_scan_u32(c, lane);
+        if (lane < NW) m.wbase[lane] = incl - c;
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        uint64_t excl = 0;
+        if (a.nslices > 1) excl = lookback(P, a, s, total, lane);
+        if (lane == 0) {
+            m.excl = excl;
+            m.total = total;
+        }
+    }
+    __syncthreads();
+
+    uint32_t *stage = stage_all + warp * kStageWords;
+    uint32_t *out = a.out;
+    const uint64_t lim = a.n;
+    uint64_t base = m.excl + m.wbase[warp];
+    for (uint32_t i0 = w0; i0 < w1; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        uint32_t v = i < w1 ? bm[i] : 0u;
+        const uint32_t c = __popc(v);
+        const uint32_t incl = warp_incl_scan_u32(c, lane);
+        const uint32_t chunk = __shfl_sync(kFull, incl, 31);
+        uint32_t pos = incl - c;
+        const uint32_t val = v0 + i * 32u;
+        while (v) {
+            const uint32_t bit = __ffs(v) - 1;
+            stage[pos++] = val + bit;
+            v &= v - 1;
+        }
+        __syncwarp();
+        for (uint32_t k = lane; k < chunk; k += 32)
+            if (base + k < lim) __stcs(out + base + k, stage[k]);   // never past n, whatever the scratch held
+        base += chunk;
+        __syncwarp();
+    }
+
+    // The CTA that finishes the array's last slice writes the outcome and
+    // returns the array's scratch to its zero state for the next launch.
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t d = atomicAdd(&a.sync[SY_SLICES_DONE], 1u);
+        m.flag = (d == a.nslices - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (m.flag) {
+        __threadfence();
+        uint64_t total = m.total;
+        if (a.nslices > 1) total = ld_acquire_u64(&a.look[a.nslices - 1]) & LB_VALUE;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < a.nslices && a.nslices > 1; i += T) a.look[i] = 0;
+        if (threadIdx.x == 0) {
+            uint32_t st = BITSORT_OK;
+            if (ld_acquire_u32(&a.sync[SY_TIMEOUT]) != 0) st = BITSORT_ERR_TIMEOUT;
+            else if (ld_acquire_u32(&a.sync[SY_RANGE]) != 0) st = BITSORT_ERR_KEY_RANGE;
+            else if (total < a.n) st = BITSORT_ERR_DUPLICATE;
+            a.result->status = st;
+            a.result->reserved = 0;
+            a.result->count = total;
+            for (int k = 0; k < SY_COUNT; ++k) a.sync[k] = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ items
+template <int T>
+__device__ void item_hist(const EngineParams &P, const ArrayDesc &a, uint32_t tile, char *smem, SharedMisc &m) {
+    const uint32_t nb = a.nslices;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    for (uint32_t i = threadIdx.x; i < nb; i += T) hist[i] = 0;
+    __syncthreads();
+    const uint64_t lo = (uint64_t)tile * a.tile_keys;
+    const uint64_t hi = min(lo + a.tile_keys, a.n);
+    bool bad = false;
+    const uint64_t M = a.M, magic = a.div_magic;
+    for_each_key<T, false>(a.keys, lo, hi, [&](uint32_t x) {
+        if ((uint64_t)x < M) atomicAdd(&hist[bucket_of(x, magic)], 1u);
+        else bad = true;
+    });
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
+    for (uint32_t i = threadIdx.x; i < nb; i += T) {
+        const uint32_t c = hist[i];
+        if (c) atomicAdd(&a.counts[i], c);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t d = atomicAdd(&a.sync[SY_HIST_DONE], 1u);
+        m.flag = (d == a.key_tiles - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (m.flag) {
+        __threadfence();
+        block_exclusive_scan<T>(
+            nb, [&](uint32_t i) -> uint64_t { return __ldcg(&a.counts[i]); },
+            [&](uint32_t i, uint64_t v) { a.offsets[i] = v; }, m);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release_u32(&a.sync[SY_OFFSETS_READY], 1u);
+    }
+}
+
+template <int T>
+__device__ void item_part(const EngineParams &P, const ArrayDesc &a, uint32_t tile, char *smem, SharedMisc &m) {
+    constexpr int K = kKeysPerThread;
+    const uint32_t nb = a.nslices;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *lpre = hist + nb;
+    uint64_t *gpos = reinterpret_cast<uint64_t *>(lpre + nb);
+    uint32_t *sorted = reinterpret_cast<uint32_t *>(gpos + nb);
+
+    if (threadIdx.x == 0)
+        m.flag = wait_geq(&a.sync[SY_OFFSETS_READY], 1u, &a.sync[SY_TIMEOUT], P.wait_limit_ns) ? 1u : 0u;
+    for (uint32_t i = threadIdx.x; i < nb; i += T) hist[i] = 0;
+    __syncthreads();
+    if (m.flag) {
+        const uint64_t lo = (uint64_t)tile * a.tile_keys;
+        const uint64_t hi = min(lo + a.tile_keys, a.n);
+        const uint64_t M = a.M, magic = a.div_magic;
+        uint32_t x[K], r[K];
+        uint32_t valid = 0;
+        const bool vec = (reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0;
+        if (vec) {
+#pragma unroll
+            for (int j = 0; j < K / 4; ++j) {
+                const uint64_t e = lo + (((uint64_t)j * T + threadIdx.x) << 2);
+                if (e + 4 <= hi) {
+                    const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(a.keys + e));
+                    x[4 * j] = q.x; x[4 * j + 1] = q.y; x[4 * j + 2] = q.z; x[4 * j + 3] = q.w;
+                    valid |= 0xFu << (4 * j);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        x[4 * j + k] = 0;
+                        if (e + k < hi) {
+                            x[4 * j + k] = __ldcs(a.keys + e + k);
+                            valid |= 1u << (4 * j + k);
+                        }
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const uint64_t e = lo + (uint64_t)j * T + threadIdx.x;
+                x[j] = 0;
+                if (e < hi) {
+                    x[j] = __ldcs(a.keys + e);
+                    valid |= 1u << j;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            r[j] = 0;
+            if ((valid >> j) & 1u) {
+                if ((uint64_t)x[j] < M) r[j] = atomicAdd(&hist[bucket_of(x[j], magic)], 1u);
+                else valid &= ~(1u << j);
+            }
+        }
+        __syncthreads();
+        const uint64_t total = block_exclusive_scan<T>(
+            nb, [&](uint32_t i) -> uint64_t { return hist[i]; },
+            [&](uint32_t i, uint64_t v) { lpre[i] = (uint32_t)v; }, m);
+        for (uint32_t i = threadIdx.x; i < nb; i += T) {
+            const uint32_t c = hist[i];
+            if (c) gpos[i] = __ldcg(&a.offsets[i]) + atomicAdd(&a.cursor[i], c);
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if ((valid >> j) & 1u) sorted[lpre[bucket_of(x[j], magic)] + r[j]] = x[j];
+        __syncthreads();
+        uint32_t *part = a.part;
+        const uint64_t lim = a.n;
+        for (uint32_t i = threadIdx.x; i < (uint32_t)total; i += T) {
+            const uint32_t v = sorted[i];
+            const uint32_t b = bucket_of(v, magic);
+            const uint64_t dst = gpos[b] + (i - lpre[b]);
+            if (dst < lim) part[dst] = v;
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(&a.sync[SY_TIMEOUT], 1u);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&a.sync[SY_PART_DONE], 1u);
+}
+
+template <int T>
+__device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t b, char *smem, SharedMisc &m) {
+    constexpr int NW = T / 32;
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *bm = stage + NW * kStageWords;
+    const uint64_t v0 = (uint64_t)b * a.S;
+    const uint64_t vals = min((uint64_t)a.S, a.M - v0);
+    const uint32_t words = (uint32_t)((vals + 31) >> 5);
+    const uint32_t w4 = (words + 3u) & ~3u;
+    const bool partitioned = a.path == BITSORT_PATH_PARTITION;
+
+    if (threadIdx.x == 0) {
+        m.flag = 1u;
+        if (partitioned)
+            m.flag = wait_geq(&a.sync[SY_PART_DONE], a.key_tiles + a.stall, &a.sync[SY_TIMEOUT], P.wait_limit_ns)
+                         ? 1u : 0u;
+    }
+    uint4 *bm4 = reinterpret_cast<uint4 *>(bm);
+    for (uint32_t i = threadIdx.x; i < w4 / 4; i += T) bm4[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    bool bad = false;
+    if (m.flag) {
+        if (partitioned) {
+            const uint64_t start = min(__ldcg(&a.offsets[b]), a.n);
+            const uint64_t cnt = min((uint64_t)__ldcg(&a.counts[b]), a.n - start);
+            const uint32_t base = (uint32_t)v0, span = (uint32_t)vals;
+            for_each_key<T, true>(a.part, start, start + cnt, [&](uint32_t x) {
+                const uint32_t l = x - base;
+                if (l < span) atomicOr(&bm[l >> 5], 1u << (l & 31));
+            });
+        } else {
+            const uint64_t M = a.M;
+            for_each_key<T, true>(a.keys, 0, a.n, [&](uint32_t x) {
+                if ((uint64_t)x < M) atomicOr(&bm[x >> 5], 1u << (x & 31));
+                else bad = true;
+            });
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(&a.sync[SY_TIMEOUT], 1u);
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
+    if (partitioned && threadIdx.x == 0) {
+        a.counts[b] = 0;
+        a.cursor[b] = 0;
+    }
+    slice_finish<T>(P, a, b, bm, words, (uint32_t)v0, stage, m);
+}
+
+template <int T>
+__device__ void item_gscatter(const EngineParams &P, const ArrayDesc &a, uint32_t tile, SharedMisc &m) {
+    const uint64_t lo = (uint64_t)tile * a.tile_keys;
+    const uint64_t hi = min(lo + a.tile_keys, a.n);
+    const uint64_t M = a.M;
+    uint32_t *bitmap = a.bitmap;
+    bool bad = false;
+    for_each_key<T, true>(a.keys, lo, hi, [&](uint32_t x) {
+        if ((uint64_t)x < M) atomicOr(&bitmap[x >> 5], 1u << (x & 31));
+        else bad = true;
+    });
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&a.sync[SY_PART_DONE], 1u);
+}
+
+template <int T>
+__device__ void item_gscan(const EngineParams &P, const ArrayDesc &a, uint32_t s, char *smem, SharedMisc &m) {
+    constexpr int NW = T / 32;
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *bm = stage + NW * kStageWords;
+    const uint64_t v0 = (uint64_t)s * a.S;
+    const uint64_t vals = min((uint64_t)a.S, a.M - v0);
+    const uint32_t words = (uint32_t)((vals + 31) >> 5);
+    const uint32_t w4 = (words + 3u) & ~3u;
+    if (threadIdx.x == 0)
+        m.flag = wait_geq(&a.sync[SY_PART_DONE], a.key_tiles + a.stall, &a.sync[SY_TIMEOUT], P.wait_limit_ns) ? 1u
+                                                                                                              : 0u;
+    __syncthreads();
+    uint4 *bm4 = reinterpret_cast<uint4 *>(bm);
+    uint4 *src = reinterpret_cast<uint4 *>(a.bitmap + (v0 >> 5));
+    if (m.flag) {
+        for (uint32_t i = threadIdx.x; i < w4 / 4; i += T) {
+            bm4[i] = __ldcg(src + i);
+            __stcg(src + i, make_uint4(0, 0, 0, 0));  // clean behind: zero for the next call
+        }
+    } else {
+        for (uint32_t i = threadIdx.x; i < w4 / 4; i += T) bm4[i] = make_uint4(0, 0, 0, 0);
+        if (threadIdx.x == 0) atomicOr(&a.sync[SY_TIMEOUT], 1u);
+    }
+    __syncthreads();
+    // words past the array's last value are zero in the bitmap (padding)
+    slice_finish<T>(P, a, s, bm, words, (uint32_t)v0, stage, m);
+}
+
+// ----------------------------------------------------------------- kernel
+template <int T>
+__global__ void __launch_bounds__(T) engine_kernel(const __grid_constant__ EngineParams P) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ SharedMisc m;
+    const Segment *segs = P.segments ? P.segments : P.seg;
+    for (;;) {
+        if (threadIdx.x == 0) m.ticket = atomicAdd(&P.ticket[0], 1u);
+        __syncthreads();
+        const uint32_t t = m.ticket;
+        __syncthreads();
+        if (t >= P.total_items) break;
+        uint32_t lo = 0, hi = P.nseg;  // last segment with start <= t
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (segs[mid].start <= t) lo = mid;
+            else hi = mid;
+        }
+        const Segment sg = segs[lo];
+        const ArrayDesc &a = P.arrays ? P.arrays[sg.array] : P.one;
+        const uint32_t idx = sg.first + (t - sg.start);
+        switch (sg.type) {
+            case IT_HIST: item_hist<T>(P, a, idx, smem, m); break;
+            case IT_PART: item_part<T>(P, a, idx, smem, m); break;
+            case IT_BUCKET: item_bucket<T>(P, a, idx, smem, m); break;
+            case IT_GSCATTER: item_gscatter<T>(P, a, idx, m); break;
+            case IT_GSCAN: item_gscan<T>(P, a, idx, smem, m); break;
+            default: break;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&P.ticket[1], 1u) == gridDim.x - 1) {
+            P.ticket[0] = 0;
+            P.ticket[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------- host
+int engine_set_smem_limit(int threads, uint32_t smem_bytes) {
+    cudaError_t e;
+    if (threads == 256) e = cudaFuncSetAttribute(engine_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    else if (threads == 512) e = cudaFuncSetAttribute(engine_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    else return (int)cudaErrorInvalidValue;
+    return (int)e;
+}
+
+int engine_max_blocks_per_sm(int threads, uint32_t smem_bytes, int *blocks) {
+    cudaError_t e;
+    if (threads == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, engine_kernel<256>, 256, smem_bytes);
+    else if (threads == 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, engine_kernel<512>, 512, smem_bytes);
+    else return (int)cudaErrorInvalidValue;
+    return (int)e;
+}
+
+int engine_launch(const EngineParams &p, int threads, uint32_t smem_bytes, int grid, void *stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (threads == 256) engine_kernel<256><<<grid, 256, smem_bytes, s>>>(p);
+    else if (threads == 512) engine_kernel<512><<<grid, 512, smem_bytes, s>>>(p);
+    else return (int)cudaErrorInvalidValue;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace bsx

@@ -1,0 +1,113 @@
+// engine.h -- device-side data layout shared by the engine kernel (engine.cu)
+// and the host code that plans and launches it (api.cu, server.cpp).
+//
+// The sort of one array (the paper's bitwise sort, Section V, in its bit-set
+// form) is split into work items, all executed by one persistent kernel that
+// takes items from a ticket counter in ascending order:
+//
+//   HIST      count the keys of one tile per bucket (bucket = the value range
+//             [b*S, (b+1)*S) of the array's bitmap); the last HIST tile of an
+//             array turns the counts into bucket offsets.
+//   PART      move the keys of one tile to their bucket's range of the
+//             partition buffer.
+//   BUCKET    build bucket b's bitmap slice in shared memory (OR of shifted
+//             ones, Table I / Example 2), count its set bits (Example 6),
+//             get the number of set bits of all earlier slices by a decoupled
+//             look-back, and write the set-bit positions to the output.  An
+//             array of one bucket is sorted by one BUCKET item straight from
+//             its input (the fused path).
+//   GSCATTER  OR the keys of one tile into a global bitmap (atomics in L2).
+//   GSCAN     load a slice of the global bitmap into shared memory, zero it
+//             behind (so the bitmap is clean for the next call), then count,
+//             look back and write out like BUCKET.
+//
+// An item only ever waits for items with smaller tickets, and every wait is
+// bounded in time, so the kernel always terminates.
+#pragma once
+#include <stdint.h>
+#include "../../include/bitsort.h"
+
+namespace bsx {
+
+enum ItemType : uint32_t { IT_HIST = 0, IT_PART = 1, IT_BUCKET = 2, IT_GSCATTER = 3, IT_GSCAN = 4 };
+
+enum SyncSlot : uint32_t {
+    SY_HIST_DONE = 0,     // HIST tiles finished
+    SY_OFFSETS_READY = 1, // bucket offsets published
+    SY_PART_DONE = 2,     // PART (or GSCATTER) tiles finished
+    SY_RANGE = 3,         // a key above max_value was seen
+    SY_TIMEOUT = 4,       // a bounded wait ran out
+    SY_SLICES_DONE = 5,   // BUCKET / GSCAN items finished
+    SY_COUNT = 8
+};
+
+// Look-back status word: flag in bits 62..63, value in bits 0..61.
+constexpr uint64_t LB_AGG = 1ull << 62;
+constexpr uint64_t LB_PREFIX = 2ull << 62;
+constexpr uint64_t LB_VALUE = (1ull << 62) - 1;
+
+// Per-array descriptor, 16-byte aligned (kernel parameter or device table).
+struct __align__(16) ArrayDesc {
+    const uint32_t *keys;
+    uint32_t *out;
+    uint32_t *part;             // partition buffer (n entries; may alias out)
+    uint32_t *bitmap;           // global bitmap (GLOBAL path), ceil(M/32) words, zero on entry
+    uint32_t *counts;           // [nslices] keys per bucket (zero on entry)
+    uint32_t *cursor;           // [nslices] reservation cursor (zero on entry)
+    uint64_t *offsets;          // [nslices] first partition-buffer index of each bucket
+    uint64_t *look;             // [nslices] look-back status (zero on entry)
+    uint32_t *sync;             // [SY_COUNT] counters (zero on entry)
+    bitsort_result_t *result;   // outcome
+    uint64_t n;
+    uint64_t M;                 // max_value + 1
+    uint64_t div_magic;         // ceil(2^64 / S): bucket of x = mulhi(x, div_magic)
+    uint32_t S;                 // values per slice, a multiple of 32
+    uint32_t nslices;           // buckets (PARTITION/FUSED) or scan tiles (GLOBAL)
+    uint32_t tile_keys;         // keys per HIST/PART/GSCATTER tile
+    uint32_t key_tiles;         // number of such tiles
+    uint32_t path;              // bitsort_path_t
+    uint32_t stall;             // extra never-scheduled PART tiles (failure-path test)
+};
+
+// A run of `count` consecutive tickets that all belong to one (array, type).
+struct Segment {
+    uint32_t start;  // first ticket
+    uint32_t array;
+    uint32_t type;
+    uint32_t first;  // index of the first item within the array's items of this type
+};
+
+constexpr int kInlineSegments = 4;
+
+struct EngineParams {
+    const ArrayDesc *arrays;       // device table, or nullptr: use `one`
+    const Segment *segments;       // device table, or nullptr: use `seg`
+    uint32_t nseg;
+    uint32_t total_items;
+    uint32_t *ticket;              // [0] next ticket, [1] finished CTAs (zero on entry)
+    uint64_t wait_limit_ns;
+    ArrayDesc one;
+    Segment seg[kInlineSegments];
+};
+
+// Shared-memory sizes (bytes) an item type needs for a given configuration.
+constexpr uint32_t kStageWords = 1024;  // per warp: 32 words x 32 bits
+inline uint32_t slice_smem_bytes(uint32_t S, int threads) {
+    uint32_t words = (S + 31) / 32;
+    uint32_t w4 = (words + 3) & ~3u;
+    return w4 * 4 + (uint32_t)(threads / 32) * kStageWords * 4;
+}
+inline uint32_t part_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
+    return nslices * 16u + tile_keys * 4u;
+}
+inline uint32_t hist_smem_bytes(uint32_t nslices) { return nslices * 4u; }
+
+constexpr int kKeysPerThread = 16;   // keys per thread in one HIST/PART/GSCATTER tile
+constexpr uint32_t kMaxSlices = 8192;
+
+// Host-side launch entry points (engine.cu).
+int engine_launch(const EngineParams &p, int threads, uint32_t smem_bytes, int grid, void *stream);
+int engine_max_blocks_per_sm(int threads, uint32_t smem_bytes, int *blocks);
+int engine_set_smem_limit(int threads, uint32_t smem_bytes);
+
+}  // namespace bsx

@@ -1,0 +1,74 @@
+// internal.h -- host-side state shared by api.cu, batch.cu and server.cpp.
+#pragma once
+#include <stdint.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bitsort.h"
+#include "engine.h"
+
+// One tuned or default configuration of the sort of one array.
+struct bsx_config {
+    bitsort_path_t path = BITSORT_PATH_PARTITION;
+    uint32_t S = 1u << 18;   // values per shared-memory slice (multiple of 128)
+    int threads = 512;       // block size of the engine kernel
+    double ms = 0;           // measured time when tuned (0 = not measured)
+};
+
+struct bitsort_ctx {
+    int device = 0;
+    int sms = 0;
+    size_t l2_bytes = 0;
+    uint32_t smem_optin = 0;
+    uint64_t wait_limit_ns = 0;
+
+    // fixed scratch: ticket/sync/result block and per-slice arrays (zero at rest)
+    void *fixed = nullptr;
+    size_t fixed_bytes = 0;
+    uint32_t *ticket = nullptr;
+    uint32_t *sync = nullptr;
+    bitsort_result_t *result = nullptr;
+    uint32_t *counts = nullptr;
+    uint32_t *cursor = nullptr;
+    uint64_t *offsets = nullptr;
+    uint64_t *look = nullptr;
+
+    // grown on demand
+    uint32_t *part = nullptr;     // partition buffer for in-place sorts
+    uint64_t part_cap = 0;
+    uint32_t *bitmap = nullptr;   // global bitmap (zero at rest)
+    uint64_t bitmap_words = 0;
+    void *flush = nullptr;        // L2 flush buffer for tuning
+    size_t flush_bytes = 0;
+
+    std::mutex mu;
+    std::map<std::pair<int, int>, bsx_config> table;  // (ceil log2 n, ceil log2 M) -> config
+    std::atomic<uint64_t> launches{0};
+};
+
+bitsort_status_t bsx_check(cudaError_t e);
+bitsort_ctx *bsx_default_ctx();
+uint64_t bsx_div_magic(uint32_t S);
+bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M);
+bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M);
+bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M);
+uint32_t bsx_smem_for(const bsx_config &cfg, uint32_t nslices, uint32_t tile_keys);
+void bsx_describe(const bsx_config &cfg, const uint32_t *keys, uint32_t *out, uint64_t n, uint64_t M,
+                  bsx::ArrayDesc &a);
+bool bsx_ranges_overlap(const void *a, const void *b, uint64_t bytes);
+int bsx_grid_for(bitsort_ctx *c, int threads, uint32_t smem, uint32_t items);
+bitsort_status_t bsx_validate(const uint32_t *keys, uint64_t n, uint32_t max_value, const uint32_t *out);
+bitsort_status_t bsx_reset_scratch(bitsort_ctx *c);
+
+// batch plans (batch.cu)
+bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, size_t count,
+                                bitsort_result_t *d_results_user, cudaStream_t stream, bool async_alloc,
+                                bitsort_batch_plan **out);
+bitsort_status_t bsx_plan_launch_direct(bitsort_batch_plan *pl, cudaStream_t s);
+void bsx_plan_release_async(bitsort_batch_plan *pl, cudaStream_t s);
+const bitsort_result_t *bsx_plan_results_ptr(const bitsort_batch_plan *pl);
