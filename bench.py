@@ -207,6 +207,7 @@ def run_plain(args, w, ws, rank, local):
 
     dev = local if torch.cuda.is_available() else 0
     torch.cuda.set_device(dev)
+    torch.cuda.set_stream(torch.cuda.Stream())   # a non-default stream: phases chain by programmatic launch
     bs.load()
     ctx = bs.Context(dev)
     keys_np = make_keys(w, rank)
@@ -216,7 +217,8 @@ def run_plain(args, w, ws, rank, local):
     if args.tune:
         ctx.autotune(keys, M - 1, out=out)
     if args.path:
-        ctx.set_config(n, M - 1, {"fused": 1, "partition": 2, "global": 3}[args.path], args.slice, args.threads)
+        ctx.set_config(n, M - 1, {"fused": 1, "partition": 2, "global": 3}[args.path], args.slice, args.threads,
+                       words_per_lane=args.wpl, stage=args.stage, layout=args.layout, persistent=args.persistent)
     cfg = ctx.get_config(n, M - 1)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -298,8 +300,7 @@ def run_plain(args, w, ws, rank, local):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": w["desc"], "n": n, "max_value": M - 1, "keys": w["method"],
                    "l2": "flushed between timed steps (512 MiB write, outside the step events)",
-                   "path": cfg["path"], "slice_values": cfg["slice_values"], "threads": cfg["threads"],
-                   "wall_s": wall},
+                   "plan": cfg, "wall_s": wall},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "note": f"algorithmic bytes 8n+M/4 = {algo_bytes} per launch (keys in, bitmap "
@@ -429,6 +430,10 @@ def main():
     ap.add_argument("--path", default=None, choices=[None, "fused", "partition", "global"])
     ap.add_argument("--slice", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--wpl", type=int, default=0)
+    ap.add_argument("--stage", type=int, default=0)
+    ap.add_argument("--layout", type=int, default=1)
+    ap.add_argument("--persistent", type=int, default=0)
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)

@@ -88,6 +88,12 @@ bitsort_status_t bitsort_ctx_destroy(bitsort_ctx_t *ctx);
 /* Text for a status code (static storage). */
 const char *bitsort_status_string(bitsort_status_t status);
 
+/* Description of the last CUDA error this thread's calls ran into ("" if
+ * none), for reports next to BITSORT_ERR_CUDA / BITSORT_ERR_NOMEM.  Thread-
+ * local storage, valid until the thread's next library call.  Setting the
+ * environment variable BITSORT_VERBOSE also prints each one to stderr. */
+const char *bitsort_last_error(void);
+
 /* ------------------------------------------------------------- single sort */
 
 /* Sort n distinct uint32 keys bounded by max_value (Algorithm 1's problem,
@@ -185,31 +191,59 @@ bitsort_status_t bitsort_server_destroy(bitsort_server_t *server);
 /* Strategies a plan may use for one array. */
 typedef enum {
     BITSORT_PATH_AUTO = 0,
-    BITSORT_PATH_FUSED = 1,     /* one CTA, bitmap in shared memory (M <= slice) */
+    BITSORT_PATH_FUSED = 1,     /* one CTA, bitmap in shared memory (M <= 2^20) */
     BITSORT_PATH_PARTITION = 2, /* high-bit partition, one shared-memory slice per bucket */
     BITSORT_PATH_GLOBAL = 3     /* atomicOr into a global (L2-resident) bitmap, then scan */
 } bitsort_path_t;
 
-/* Time the candidate configurations (path x slice size x block size) on
- * representative DEVICE data: n distinct keys bounded by max_value in `keys`
- * (left unchanged) and a separate DEVICE buffer `out` of n elements (keys and
- * out must not overlap).  Each candidate runs once to warm up, then five
- * times with L2 flushed in between; the one with the smallest median time
- * goes into the context's table for the size class (ceil(log2 n),
- * ceil(log2 M)) and is reported (pointers nullable).  Synchronises. */
-bitsort_status_t bitsort_autotune(bitsort_ctx_t *ctx, const uint32_t *keys, uint32_t *out, uint64_t n,
-                                  uint32_t max_value, bitsort_path_t *path, uint32_t *slice_values,
-                                  uint32_t *block_threads, double *best_ms);
+/* One configuration of the sort of one array.
+ *   path            see bitsort_path_t.
+ *   slice_values    values per shared-memory bitmap slice (bucket or scan
+ *                   tile), a multiple of 128, at most 2^20.
+ *   block_threads   256 or 512.
+ *   words_per_lane  bitmap words each lane takes per scan step: 1, 2 or 4.
+ *   stage           1: set-bit positions are staged per warp in shared
+ *                   memory and leave in coalesced stores (words_per_lane 1).
+ *   layout          PARTITION path: 0 = exact bucket ranges from a histogram
+ *                   pass (n-entry buffer, the output buffer when it does not
+ *                   alias the keys); 1 = fixed capacity min(slice, n) per
+ *                   bucket in a context buffer, no histogram pass.
+ *   persistent      1: all phases in one persistent launch; 0: one kernel
+ *                   per phase.
+ *   ms              measured time when tuned (output only). */
+typedef struct {
+    int32_t path;
+    uint32_t slice_values;
+    uint32_t block_threads;
+    uint32_t words_per_lane;
+    uint32_t stage;
+    uint32_t layout;
+    uint32_t persistent;
+    uint32_t reserved;
+    double ms;
+} bitsort_config_t;
 
-/* Force a configuration for the size class of (n, max_value) (testing and
- * benchmarking): path, values per shared-memory slice (a multiple of 32; 0 =
- * default) and threads per block (256 or 512; 0 = default). */
-bitsort_status_t bitsort_set_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max_value, bitsort_path_t path,
-                                    uint32_t slice_values, uint32_t block_threads);
+/* Time the candidate configurations on representative DEVICE data: n
+ * distinct keys bounded by max_value in `keys` (left unchanged) and a
+ * separate DEVICE buffer `out` of n elements (keys and out must not
+ * overlap).  Each candidate runs once to warm up, then five times with L2
+ * flushed in between; the one with the smallest median time goes into the
+ * context's table for the size class (ceil(log2 n), ceil(log2 M)) and is
+ * reported in *best (nullable).  Synchronises the device. */
+bitsort_status_t bitsort_autotune(bitsort_ctx_t *ctx, const uint32_t *keys, uint32_t *out, uint64_t n,
+                                  uint32_t max_value, bitsort_config_t *best);
+
+/* Force a configuration for the size class of (n, max_value).  slice_values,
+ * block_threads and words_per_lane left 0 take the default; stage, layout
+ * and persistent are taken as given; path BITSORT_PATH_AUTO removes the
+ * entry (back to the built-in rule).  The
+ * configuration is adjusted to what the size allows (e.g. no fused path
+ * beyond 2^20 values, at most 8192 slices). */
+bitsort_status_t bitsort_set_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max_value,
+                                    const bitsort_config_t *config);
 
 /* The configuration the context would use for (n, max_value). */
-bitsort_status_t bitsort_get_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max_value, bitsort_path_t *path,
-                                    uint32_t *slice_values, uint32_t *block_threads);
+bitsort_status_t bitsort_get_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max_value, bitsort_config_t *config);
 
 /* Save / load the tuned table as JSON text at `path`. */
 bitsort_status_t bitsort_tune_save(bitsort_ctx_t *ctx, const char *path);

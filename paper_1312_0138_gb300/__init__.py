@@ -30,7 +30,8 @@ PATH_NAMES = {0: "auto", 1: "fused", 2: "partition", 3: "global"}
 
 # names every build must export (checked by the CPU test-suite)
 EXPORTS = [
-    "bitsort_ctx_create", "bitsort_ctx_destroy", "bitsort_status_string", "bitsort", "bitsort_ex",
+    "bitsort_ctx_create", "bitsort_ctx_destroy", "bitsort_status_string", "bitsort_last_error", "bitsort",
+    "bitsort_ex",
     "bitsort_sync_status", "bitsort_batched", "bitsort_batch_plan_create", "bitsort_batch_plan_launch",
     "bitsort_batch_plan_results", "bitsort_batch_plan_device_results", "bitsort_batch_plan_destroy",
     "bitsort_server_create", "bitsort_server_submit", "bitsort_server_wait", "bitsort_server_stats",
@@ -48,6 +49,22 @@ class BitsortError(RuntimeError):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("count", ctypes.c_uint64)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("slice_values", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("words_per_lane", ctypes.c_uint32), ("stage", ctypes.c_uint32), ("layout", ctypes.c_uint32),
+                ("persistent", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"path": PATH_NAMES.get(self.path, self.path), "slice_values": self.slice_values,
+                "threads": self.block_threads, "words_per_lane": self.words_per_lane, "stage": self.stage,
+                "layout": LAYOUT_NAMES.get(self.layout, self.layout), "persistent": self.persistent,
+                "ms": self.ms}
+
+
+LAYOUT_EXACT, LAYOUT_CAPACITY = 0, 1
+LAYOUT_NAMES = {0: "exact", 1: "capacity"}
 
 
 class Desc(ctypes.Structure):
@@ -71,6 +88,7 @@ def _declare(lib):
         "bitsort_ctx_create": (st, [i32, ctypes.POINTER(p)]),
         "bitsort_ctx_destroy": (st, [p]),
         "bitsort_status_string": (ctypes.c_char_p, [i32]),
+        "bitsort_last_error": (ctypes.c_char_p, []),
         "bitsort": (st, [p, ctypes.c_size_t, u32, p, p]),
         "bitsort_ex": (st, [p, p, u64, u32, p, p, p]),
         "bitsort_sync_status": (st, [p, p, ctypes.POINTER(u64)]),
@@ -86,11 +104,9 @@ def _declare(lib):
                                      ctypes.POINTER(ctypes.c_double)]),
         "bitsort_server_stats": (st, [p] + [ctypes.POINTER(u64)] * 4),
         "bitsort_server_destroy": (st, [p]),
-        "bitsort_autotune": (st, [p, p, p, u64, u32, ctypes.POINTER(i32), ctypes.POINTER(u32),
-                                  ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_double)]),
-        "bitsort_set_config": (st, [p, u64, u32, i32, u32, u32]),
-        "bitsort_get_config": (st, [p, u64, u32, ctypes.POINTER(i32), ctypes.POINTER(u32),
-                                    ctypes.POINTER(u32)]),
+        "bitsort_autotune": (st, [p, p, p, u64, u32, ctypes.POINTER(Config)]),
+        "bitsort_set_config": (st, [p, u64, u32, ctypes.POINTER(Config)]),
+        "bitsort_get_config": (st, [p, u64, u32, ctypes.POINTER(Config)]),
         "bitsort_tune_save": (st, [p, ctypes.c_char_p]),
         "bitsort_tune_load": (st, [p, ctypes.c_char_p]),
         "bitsort_set_wait_limit_ms": (st, [p, u32]),
@@ -118,7 +134,10 @@ def load(path: Optional[str] = None):
 
 def _check(status: int, what: str):
     if status != OK:
-        raise BitsortError(status, what)
+        detail = ""
+        if status in (ERR_CUDA, ERR_NOMEM) and _lib is not None:
+            detail = " [" + (_lib.bitsort_last_error() or b"").decode(errors="replace") + "]"
+        raise BitsortError(status, what + detail)
 
 
 def _stream_handle(stream) -> int:
@@ -190,25 +209,24 @@ class Context:
         return st, cnt, out
 
     # tuning ----------------------------------------------------------------
-    def set_config(self, n: int, max_value: int, path: int, slice_values: int = 0, threads: int = 0):
-        _check(load().bitsort_set_config(self.handle, n, max_value, path, slice_values, threads),
-               "bitsort_set_config")
+    def set_config(self, n: int, max_value: int, path: int, slice_values: int = 0, threads: int = 0,
+                   words_per_lane: int = 0, stage: int = 0, layout: int = LAYOUT_CAPACITY, persistent: int = 0):
+        cfg = Config(path, slice_values, threads, words_per_lane, stage, layout, persistent, 0, 0.0)
+        _check(load().bitsort_set_config(self.handle, n, max_value, ctypes.byref(cfg)), "bitsort_set_config")
 
     def get_config(self, n: int, max_value: int):
-        p, s, t = ctypes.c_int(0), ctypes.c_uint32(0), ctypes.c_uint32(0)
-        _check(load().bitsort_get_config(self.handle, n, max_value, ctypes.byref(p), ctypes.byref(s),
-                                         ctypes.byref(t)), "bitsort_get_config")
-        return {"path": PATH_NAMES[p.value], "slice_values": s.value, "threads": t.value}
+        cfg = Config()
+        _check(load().bitsort_get_config(self.handle, n, max_value, ctypes.byref(cfg)), "bitsort_get_config")
+        return cfg.as_dict()
 
     def autotune(self, keys, max_value: int, out=None):
         import torch
         if out is None:
             out = torch.empty_like(keys)
-        p, s, t, ms = ctypes.c_int(0), ctypes.c_uint32(0), ctypes.c_uint32(0), ctypes.c_double(0)
+        cfg = Config()
         _check(load().bitsort_autotune(self.handle, _ptr(keys), _ptr(out), keys.numel(), int(max_value),
-                                       ctypes.byref(p), ctypes.byref(s), ctypes.byref(t), ctypes.byref(ms)),
-               "bitsort_autotune")
-        return {"path": PATH_NAMES[p.value], "slice_values": s.value, "threads": t.value, "ms": ms.value}
+                                       ctypes.byref(cfg)), "bitsort_autotune")
+        return cfg.as_dict()
 
     def tune_save(self, path: str):
         _check(load().bitsort_tune_save(self.handle, path.encode()), "bitsort_tune_save")

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -32,6 +33,7 @@ using namespace bsx;
 namespace {
 
 constexpr uint32_t kMaxSliceValues = 1u << 20;   // 128 KiB of bitmap per CTA
+constexpr uint64_t kCapacityScratchMax = 4ull << 30;  // largest CAPACITY partition buffer (bytes)
 constexpr uint64_t kDefaultWaitNs = 4000ull * 1000ull * 1000ull;
 
 inline uint32_t round_up_u32(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
@@ -46,7 +48,18 @@ inline int ilog2_ceil(uint64_t v) {
 }  // namespace
 
 // ---------------------------------------------------------------- context
+static thread_local char g_last_error[256] = "";
+
+void bsx_note_error(int e, const char *where) {
+    if (e == 0) return;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString((cudaError_t)e), e);
+    if (getenv("BITSORT_VERBOSE")) fprintf(stderr, "bitsort: %s\n", g_last_error);
+}
+
+extern "C" const char *bitsort_last_error(void) { return g_last_error; }
+
 bitsort_status_t bsx_check(cudaError_t e) {
+    if (e != cudaSuccess) bsx_note_error((int)e, "CUDA runtime");
     if (e == cudaSuccess) return BITSORT_OK;
     if (e == cudaErrorMemoryAllocation) return BITSORT_ERR_NOMEM;
     return BITSORT_ERR_CUDA;
@@ -156,20 +169,25 @@ uint64_t bsx_div_magic(uint32_t S) {
 
 bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M) {
     bsx_config cfg;
-    cfg.threads = 512;
+    cfg.threads = 256;
+    cfg.wpl = 2;
+    cfg.stage = false;
     if (M <= (1ull << 17) || (M <= kMaxSliceValues && n <= (1ull << 16))) {
         cfg.path = BITSORT_PATH_FUSED;
+        cfg.threads = 512;
         cfg.S = round_up_u32((uint32_t)M, 128);
         return cfg;
     }
     cfg.path = BITSORT_PATH_PARTITION;
-    uint64_t target = 2ull * (uint64_t)c->sms;
+    cfg.layout = LAYOUT_CAPACITY;
+    // about four slices per SM: four CTAs of 256 threads fit one SM
+    uint64_t target = 4ull * (uint64_t)c->sms;
     uint64_t S = ceil_div(M, target);
     uint64_t lo = std::max<uint64_t>(4096, ceil_div(M, kMaxSlices));
     S = std::max(S, lo);
     S = std::min<uint64_t>(S, kMaxSliceValues);
     cfg.S = round_up_u32((uint32_t)S, 128);
-    return cfg;
+    return bsx_sanitize(cfg, n, M);
 }
 
 bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M) {
@@ -183,6 +201,9 @@ bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M) {
 // slice a multiple of 128 values, FUSED only where one slice covers M.
 bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
     if (cfg.threads != 256 && cfg.threads != 512) cfg.threads = 512;
+    if (cfg.wpl != 1 && cfg.wpl != 2 && cfg.wpl != 4) cfg.wpl = 2;
+    if (cfg.stage) cfg.wpl = 1;
+    if (cfg.layout != LAYOUT_EXACT && cfg.layout != LAYOUT_CAPACITY) cfg.layout = LAYOUT_EXACT;
     if (cfg.path == BITSORT_PATH_FUSED && M > kMaxSliceValues) cfg.path = BITSORT_PATH_PARTITION;
     if (cfg.path == BITSORT_PATH_FUSED) {
         cfg.S = round_up_u32((uint32_t)M, 128);
@@ -194,12 +215,16 @@ bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
     S = std::min<uint64_t>(S, kMaxSliceValues);
     S = std::max<uint64_t>(S, 128);
     cfg.S = round_up_u32((uint32_t)S, 128);
-    (void)n;
+    if (cfg.path == BITSORT_PATH_PARTITION && cfg.layout == LAYOUT_CAPACITY) {
+        const uint64_t nb = ceil_div(M, cfg.S);
+        const uint64_t cap = std::min<uint64_t>(cfg.S, n);
+        if (nb * cap * 4 > kCapacityScratchMax) cfg.layout = LAYOUT_EXACT;
+    }
     return cfg;
 }
 
 uint32_t bsx_smem_for(const bsx_config &cfg, uint32_t nslices, uint32_t tile_keys) {
-    uint32_t s = slice_smem_bytes(cfg.S, cfg.threads);
+    uint32_t s = slice_smem_bytes(cfg.S, cfg.threads, cfg.stage);
     if (cfg.path == BITSORT_PATH_PARTITION) {
         s = std::max(s, part_smem_bytes(nslices, tile_keys));
         s = std::max(s, hist_smem_bytes(nslices));
@@ -221,6 +246,11 @@ void bsx_describe(const bsx_config &cfg, const uint32_t *keys, uint32_t *out, ui
     a.nslices = (uint32_t)ceil_div(M, cfg.S);
     a.tile_keys = (uint32_t)(kKeysPerThread * cfg.threads);
     a.key_tiles = (uint32_t)ceil_div(n, a.tile_keys);
+    a.wpl = cfg.stage ? 1 : cfg.wpl;
+    a.stage = cfg.stage ? 1 : 0;
+    a.phased = cfg.persistent ? 0 : 1;
+    a.layout = cfg.path == BITSORT_PATH_PARTITION ? cfg.layout : LAYOUT_EXACT;
+    a.cap = a.layout == LAYOUT_CAPACITY ? std::min<uint64_t>(cfg.S, n) : 0;
     if (cfg.path == BITSORT_PATH_FUSED) {
         a.nslices = 1;
         a.key_tiles = 0;
@@ -288,7 +318,7 @@ uint32_t bsx_single_segments(const ArrayDesc &a, Segment *seg, uint32_t *nseg) {
     if (a.path == BITSORT_PATH_FUSED) {
         add(IT_BUCKET, 1);
     } else if (a.path == BITSORT_PATH_PARTITION) {
-        add(IT_HIST, a.key_tiles);
+        if (a.layout == LAYOUT_EXACT) add(IT_HIST, a.key_tiles);
         add(IT_PART, a.key_tiles);
         add(IT_BUCKET, a.nslices);
     } else {
@@ -309,7 +339,11 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     bsx_describe(cfg, keys, out, n, M, a);
     a.stall = stall;
     bool alias = keys == out;
-    if (cfg.path == BITSORT_PATH_PARTITION) {
+    if (cfg.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
+        bitsort_status_t st = ensure_part(c, (uint64_t)a.nslices * a.cap);
+        if (st != BITSORT_OK) return st;
+        a.part = c->part;
+    } else if (cfg.path == BITSORT_PATH_PARTITION) {
         if (alias) {
             bitsort_status_t st = ensure_part(c, n);
             if (st != BITSORT_OK) return st;
@@ -334,13 +368,62 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     p.total_items = bsx_single_segments(a, p.seg, &p.nseg);
     p.ticket = c->ticket;
     p.wait_limit_ns = c->wait_limit_ns;
-    uint32_t smem = bsx_smem_for(cfg, a.nslices, a.tile_keys);
-    if (smem > c->smem_optin) return BITSORT_ERR_INVALID;
-    int grid = bsx_grid_for(c, cfg.threads, smem, p.total_items);
-    int e = engine_launch(p, cfg.threads, smem, grid, stream);
-    if (e != 0) return BITSORT_ERR_CUDA;
-    c->launches.fetch_add(1);
-    return BITSORT_OK;
+    const int T = cfg.threads;
+    if (cfg.persistent) {
+        // every phase in one persistent launch (items in ticket order)
+        uint32_t smem = bsx_smem_for(cfg, a.nslices, a.tile_keys);
+        if (smem > c->smem_optin) return BITSORT_ERR_INVALID;
+        int grid = bsx_grid_for(c, T, smem, p.total_items);
+        int e = engine_launch(p, T, smem, grid, stream);
+        if (e != 0) {
+            bsx_note_error(e, "engine launch");
+            return BITSORT_ERR_CUDA;
+        }
+        c->launches.fetch_add(1);
+        return BITSORT_OK;
+    }
+    // one kernel per phase, each at the occupancy its shared memory allows;
+    // later phases use programmatic dependent launch to hide the launch gap
+    int launched = 0;
+    auto phase = [&](int kind, uint32_t items, uint32_t smem) -> bool {
+        if (items == 0) return true;
+        if (smem > c->smem_optin) {
+            bsx_note_error((int)cudaErrorInvalidValue, "shared memory above the per-block limit");
+            return false;
+        }
+        EngineParams q = p;
+        q.total_items = items;
+        int per_sm = 1;
+        if (kernel_max_blocks_per_sm(kind, T, smem, &per_sm) != 0 || per_sm < 1) per_sm = 1;
+        // slice phases and the streaming HIST / GSCATTER phases: one wave of
+        // resident CTAs; PART: a few tiles per CTA
+        const bool one_wave = kind != IT_PART;
+        uint64_t grid = (uint64_t)c->sms * (uint64_t)per_sm * (one_wave ? 1u : 8u);
+        if (grid > items) grid = items;
+        int e = kernel_launch(kind, q, T, smem, (int)grid, stream, launched > 0);
+        if (e != 0) {
+            bsx_note_error(e, "phase kernel launch");
+            return false;
+        }
+        ++launched;
+        return true;
+    };
+    const uint32_t sl = slice_smem_bytes(cfg.S, T, cfg.stage);
+    bool ok = true;
+    if (a.path == BITSORT_PATH_FUSED) {
+        ok = phase(IT_BUCKET, 1, sl);
+    } else if (a.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
+        ok = phase(IT_PART, a.key_tiles, part_smem_bytes(a.nslices, a.tile_keys)) &&
+             phase(IT_BUCKET, a.nslices, sl);
+    } else if (a.path == BITSORT_PATH_PARTITION) {
+        ok = phase(IT_HIST, a.key_tiles, hist_smem_bytes(a.nslices)) &&
+             phase(IT_PART, a.key_tiles, part_smem_bytes(a.nslices, a.tile_keys)) &&
+             phase(IT_BUCKET, a.nslices, sl);
+    } else {
+        ok = phase(IT_GSCATTER, a.key_tiles, 0) && phase(IT_GSCAN, a.nslices, sl);
+    }
+    c->launches.fetch_add((uint64_t)launched);
+    return ok ? BITSORT_OK : BITSORT_ERR_CUDA;
 }
 
 static bitsort_status_t write_trivial_result(bitsort_ctx *c, bitsort_result_t *d_result, cudaStream_t s) {
@@ -414,6 +497,8 @@ extern "C" bitsort_status_t bitsort_debug_stalled_launch(bitsort_ctx_t *c, const
     uint64_t M = (uint64_t)max_value + 1;
     bsx_config cfg;
     cfg.path = BITSORT_PATH_PARTITION;
+    cfg.layout = LAYOUT_EXACT;
+    cfg.persistent = true;  // the bucket items wait on the partition tiles inside one launch
     cfg.threads = 256;
     cfg.S = (uint32_t)std::max<uint64_t>(128, ceil_div(M, 4));  // four buckets
     return launch_single(c, cfg, keys, n, M, out, nullptr, reinterpret_cast<cudaStream_t>(stream), 1);
@@ -425,55 +510,90 @@ extern "C" uint64_t bitsort_kernel_launches(const bitsort_ctx_t *c) {
 }
 
 // --------------------------------------------------------------- tuning
-extern "C" bitsort_status_t bitsort_set_config(bitsort_ctx_t *c, uint64_t n, uint32_t max_value, bitsort_path_t path,
-                                               uint32_t slice_values, uint32_t block_threads) {
+static void to_public(const bsx_config &c, bitsort_config_t *o) {
+    o->path = (int32_t)c.path;
+    o->slice_values = c.S;
+    o->block_threads = (uint32_t)c.threads;
+    o->words_per_lane = c.wpl;
+    o->stage = c.stage ? 1 : 0;
+    o->layout = c.layout;
+    o->persistent = c.persistent ? 1 : 0;
+    o->reserved = 0;
+    o->ms = c.ms;
+}
+
+extern "C" bitsort_status_t bitsort_set_config(bitsort_ctx_t *c, uint64_t n, uint32_t max_value,
+                                               const bitsort_config_t *in) {
     if (!c) c = bsx_default_ctx();
-    if (!c) return BITSORT_ERR_CUDA;
+    if (!c || !in) return BITSORT_ERR_INVALID;
     uint64_t M = (uint64_t)max_value + 1;
     std::lock_guard<std::mutex> lk(c->mu);
     auto key = std::make_pair(ilog2_ceil(n), ilog2_ceil(M));
-    if (path == BITSORT_PATH_AUTO) {
+    if (in->path == BITSORT_PATH_AUTO) {
         c->table.erase(key);
         return BITSORT_OK;
     }
+    if (in->path < BITSORT_PATH_FUSED || in->path > BITSORT_PATH_GLOBAL) return BITSORT_ERR_INVALID;
     bsx_config cfg = bsx_default_config(c, n, M);
-    cfg.path = path;
-    if (slice_values) cfg.S = slice_values;
-    if (block_threads) cfg.threads = (int)block_threads;
+    cfg.path = (bitsort_path_t)in->path;
+    if (in->slice_values) cfg.S = in->slice_values;
+    if (in->block_threads) cfg.threads = (int)in->block_threads;
+    if (in->words_per_lane) cfg.wpl = in->words_per_lane;
+    cfg.stage = in->stage != 0;
+    cfg.layout = in->layout;
+    cfg.persistent = in->persistent != 0;
     c->table[key] = bsx_sanitize(cfg, n, M);
     return BITSORT_OK;
 }
 
-extern "C" bitsort_status_t bitsort_get_config(bitsort_ctx_t *c, uint64_t n, uint32_t max_value, bitsort_path_t *path,
-                                               uint32_t *slice_values, uint32_t *block_threads) {
+extern "C" bitsort_status_t bitsort_get_config(bitsort_ctx_t *c, uint64_t n, uint32_t max_value,
+                                               bitsort_config_t *out) {
     if (!c) c = bsx_default_ctx();
-    if (!c) return BITSORT_ERR_CUDA;
+    if (!c || !out) return BITSORT_ERR_INVALID;
     uint64_t M = (uint64_t)max_value + 1;
-    bsx_config cfg = bsx_sanitize(bsx_lookup_config(c, n, M), n, M);
-    if (path) *path = cfg.path;
-    if (slice_values) *slice_values = cfg.S;
-    if (block_threads) *block_threads = (uint32_t)cfg.threads;
+    to_public(bsx_sanitize(bsx_lookup_config(c, n, M), n, M), out);
     return BITSORT_OK;
 }
 
 // Candidate configurations for (n, M), deduplicated after sanitizing.
 std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_t M) {
     std::vector<bsx_config> out;
-    auto push = [&](bitsort_path_t path, uint64_t S, int threads) {
+    auto push = [&](bitsort_path_t path, uint64_t S, int threads, uint32_t wpl, bool stage, uint32_t layout) {
         bsx_config cfg;
         cfg.path = path;
         cfg.S = (uint32_t)std::min<uint64_t>(S, 0xFFFFFF80u);
         cfg.threads = threads;
+        cfg.wpl = wpl;
+        cfg.stage = stage;
+        cfg.layout = layout;
         cfg = bsx_sanitize(cfg, n, M);
         for (auto &o : out)
-            if (o.path == cfg.path && o.S == cfg.S && o.threads == cfg.threads) return;
+            if (o.path == cfg.path && o.S == cfg.S && o.threads == cfg.threads && o.wpl == cfg.wpl &&
+                o.stage == cfg.stage && o.layout == cfg.layout)
+                return;
         out.push_back(cfg);
     };
     for (int threads : {256, 512}) {
-        if (M <= kMaxSliceValues) push(BITSORT_PATH_FUSED, M, threads);
-        for (int k : {1, 2, 3, 4, 6, 8}) push(BITSORT_PATH_PARTITION, ceil_div(M, (uint64_t)k * c->sms), threads);
-        for (int lg : {16, 17, 18, 19, 20}) push(BITSORT_PATH_PARTITION, 1ull << lg, threads);
-        for (int lg : {14, 16, 18, 20}) push(BITSORT_PATH_GLOBAL, 1ull << lg, threads);
+        for (uint32_t wpl : {1u, 2u, 4u}) {
+            if (M <= kMaxSliceValues) push(BITSORT_PATH_FUSED, M, threads, wpl, false, LAYOUT_EXACT);
+            for (uint32_t layout : {(uint32_t)LAYOUT_EXACT, (uint32_t)LAYOUT_CAPACITY}) {
+                for (int k : {1, 2, 3, 4, 6, 8})
+                    push(BITSORT_PATH_PARTITION, ceil_div(M, (uint64_t)k * c->sms), threads, wpl, false, layout);
+                for (int lg : {16, 18, 20}) push(BITSORT_PATH_PARTITION, 1ull << lg, threads, wpl, false, layout);
+            }
+            for (int lg : {14, 16, 18, 20}) push(BITSORT_PATH_GLOBAL, 1ull << lg, threads, wpl, false, 0);
+        }
+        if (M <= kMaxSliceValues) push(BITSORT_PATH_FUSED, M, threads, 1, true, LAYOUT_EXACT);
+        for (int k : {2, 4}) {
+            bsx_config pc = bsx_sanitize(bsx_default_config(c, n, M), n, M);
+            pc.threads = threads;
+            pc.S = (uint32_t)ceil_div(M, (uint64_t)k * c->sms);
+            pc.persistent = true;
+            pc = bsx_sanitize(pc, n, M);
+            if (pc.path != BITSORT_PATH_FUSED) out.push_back(pc);
+        }
+        push(BITSORT_PATH_PARTITION, ceil_div(M, 2ull * c->sms), threads, 1, true, LAYOUT_CAPACITY);
+        push(BITSORT_PATH_PARTITION, ceil_div(M, 2ull * c->sms), threads, 1, true, LAYOUT_EXACT);
     }
     // shared memory must fit
     std::vector<bsx_config> fit;
@@ -495,8 +615,7 @@ static bitsort_status_t ensure_flush(bitsort_ctx *c) {
 }
 
 extern "C" bitsort_status_t bitsort_autotune(bitsort_ctx_t *c, const uint32_t *keys, uint32_t *out, uint64_t n,
-                                             uint32_t max_value, bitsort_path_t *path, uint32_t *slice_values,
-                                             uint32_t *block_threads, double *best_ms) {
+                                             uint32_t max_value, bitsort_config_t *best_out) {
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     bitsort_status_t st = bsx_validate(keys, n, max_value, out);
@@ -514,6 +633,9 @@ extern "C" bitsort_status_t bitsort_autotune(bitsort_ctx_t *c, const uint32_t *k
     bsx_config best_cfg = bsx_default_config(c, n, M);
     for (const bsx_config &cfg : bsx_candidates(c, n, M)) {
         // one warm-up, then the median of five cold-L2 runs
+        ArrayDesc probe;
+        bsx_describe(cfg, nullptr, nullptr, n, M, probe);
+        if (bsx_smem_for(cfg, probe.nslices, probe.tile_keys) > c->smem_optin) continue;
         if (launch_single(c, cfg, keys, n, M, out, nullptr, s, 0) != BITSORT_OK) continue;
         std::vector<float> ts;
         bool ok = true;
@@ -549,10 +671,7 @@ extern "C" bitsort_status_t bitsort_autotune(bitsort_ctx_t *c, const uint32_t *k
         best_cfg.ms = best;
         c->table[std::make_pair(ilog2_ceil(n), ilog2_ceil(M))] = best_cfg;
     }
-    if (path) *path = best_cfg.path;
-    if (slice_values) *slice_values = best_cfg.S;
-    if (block_threads) *block_threads = (uint32_t)best_cfg.threads;
-    if (best_ms) *best_ms = best;
+    if (best_out) to_public(best_cfg, best_out);
     return BITSORT_OK;
 }
 
@@ -565,9 +684,12 @@ extern "C" bitsort_status_t bitsort_tune_save(bitsort_ctx_t *c, const char *path
     fprintf(f, "{\"version\": 1, \"entries\": [");
     bool first = true;
     for (auto &kv : c->table) {
-        fprintf(f, "%s\n  {\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, \"ms\": %.6f}",
-                first ? "" : ",", kv.first.first, kv.first.second, (int)kv.second.path, kv.second.S,
-                kv.second.threads, kv.second.ms);
+        const bsx_config &g = kv.second;
+        fprintf(f,
+                "%s\n  {\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
+                "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"ms\": %.6f}",
+                first ? "" : ",", kv.first.first, kv.first.second, (int)g.path, g.S, g.threads, g.wpl,
+                g.stage ? 1 : 0, g.layout, g.persistent ? 1 : 0, g.ms);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -588,12 +710,13 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
     std::map<std::pair<int, int>, bsx_config> table;
     size_t pos = 0;
     while ((pos = text.find("{\"log2n\"", pos)) != std::string::npos) {
-        int ln = 0, lm = 0, p = 0, th = 0;
-        unsigned S = 0;
+        int ln = 0, lm = 0, p = 0, th = 0, stage = 0, pers = 0;
+        unsigned S = 0, wpl = 0, layout = 0;
         double ms = 0;
         if (sscanf(text.c_str() + pos,
-                   "{\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, \"ms\": %lf",
-                   &ln, &lm, &p, &S, &th, &ms) != 6)
+                   "{\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
+                   "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"ms\": %lf",
+                   &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &ms) != 10)
             return BITSORT_ERR_INVALID;
         if (p < 1 || p > 3 || (th != 256 && th != 512) || ln < 0 || ln > 64 || lm < 0 || lm > 33)
             return BITSORT_ERR_INVALID;
@@ -601,6 +724,10 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
         cfg.path = (bitsort_path_t)p;
         cfg.S = S;
         cfg.threads = th;
+        cfg.wpl = wpl;
+        cfg.stage = stage != 0;
+        cfg.layout = layout;
+        cfg.persistent = pers != 0;
         cfg.ms = ms;
         table[std::make_pair(ln, lm)] = cfg;
         ++pos;

@@ -248,7 +248,10 @@ extern "C" bitsort_status_t bitsort_batch_plan_create(bitsort_ctx_t *c, const bi
 bitsort_status_t bsx_plan_launch_direct(bitsort_batch_plan *pl, cudaStream_t s) {
     if (pl->params.total_items == 0) return BITSORT_OK;
     int e = engine_launch(pl->params, pl->threads, pl->smem, pl->grid, s);
-    if (e != 0) return BITSORT_ERR_CUDA;
+    if (e != 0) {
+        bsx_note_error(e, "batched engine launch");
+        return BITSORT_ERR_CUDA;
+    }
     pl->ctx->launches.fetch_add(1);
     return BITSORT_OK;
 }

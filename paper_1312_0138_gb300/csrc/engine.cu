@@ -19,6 +19,8 @@
 //     iterations, and reports a timeout instead of hanging.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include "engine.h"
 
@@ -234,19 +236,103 @@ __device__ uint64_t lookback(const EngineParams &P, const ArrayDesc &a, uint32_t
     return excl;
 }
 
+// Writes the set-bit positions of bm[w0, w1) in ascending order to
+// out[base ...]: value = v0 + 32*word + bit (Section II numbering, bit 0
+// first).  Each lane takes WPL consecutive words per step; the lanes' counts
+// are prefix-summed across the warp to place them.  STAGE: the positions of
+// a step go through a per-warp shared-memory buffer and leave in coalesced
+// stores; otherwise every lane stores its own positions (consecutive lanes
+// write neighbouring addresses, which stays coalesced at low density).
+template <int WPL, bool STAGE>
+__device__ __forceinline__ void emit_words(const uint32_t *bm, uint32_t w0, uint32_t w1, uint32_t v0, uint64_t base,
+                                           uint32_t *out, uint64_t lim, uint32_t *stage) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t i0 = w0; i0 < w1; i0 += 32 * WPL) {
+        const uint32_t i = i0 + lane * WPL;
+        uint32_t v[WPL];
+        if (i < w1) {
+            if constexpr (WPL == 4) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(bm + i);
+                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else if constexpr (WPL == 2) {
+                const uint2 q = *reinterpret_cast<const uint2 *>(bm + i);
+                v[0] = q.x; v[1] = q.y;
+            } else {
+                v[0] = bm[i];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < WPL; ++k) v[k] = 0;
+        }
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < WPL; ++k) c += __popc(v[k]);
+        const uint32_t incl = warp_incl_scan_u32(c, lane);
+        const uint32_t chunk = __shfl_sync(kFull, incl, 31);
+        uint32_t pos = incl - c;
+        if constexpr (STAGE) {
+            uint32_t val = v0 + i * 32u;
+            uint32_t x = v[0];
+            while (x) {
+                stage[pos++] = val + (__ffs(x) - 1);
+                x &= x - 1;
+            }
+            __syncwarp();
+            for (uint32_t k = lane; k < chunk; k += 32)
+                if (base + k < lim) __stcs(out + base + k, stage[k]);   // never past n, whatever the scratch held
+            __syncwarp();
+        } else {
+            uint64_t o = base + pos;
+#pragma unroll
+            for (int k = 0; k < WPL; ++k) {
+                const uint32_t val = v0 + (i + k) * 32u;
+                uint32_t x = v[k];
+                while (x) {
+                    if (o < lim) __stcs(out + o, val + (__ffs(x) - 1));
+                    ++o;
+                    x &= x - 1;
+                }
+            }
+        }
+        base += chunk;
+    }
+}
+
+template <int WPL>
+__device__ __forceinline__ uint32_t count_words(const uint32_t *bm, uint32_t w0, uint32_t w1) {
+    const int lane = threadIdx.x & 31;
+    uint32_t c = 0;
+    for (uint32_t i = w0 + lane * WPL; i < w1; i += 32 * WPL) {
+        if constexpr (WPL == 4) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(bm + i);
+            c += __popc(q.x) + __popc(q.y) + __popc(q.z) + __popc(q.w);
+        } else if constexpr (WPL == 2) {
+            const uint2 q = *reinterpret_cast<const uint2 *>(bm + i);
+            c += __popc(q.x) + __popc(q.y);
+        } else {
+            c += __popc(bm[i]);
+        }
+    }
+    return warp_sum_u32(c);
+}
+
 // Count, look back and write out one bitmap slice held in shared memory.
-// `bm` holds `words` words covering the values v0 .. v0 + 32*words - 1.
+// `bm` holds `words` words covering the values v0 .. v0 + 32*words - 1 and is
+// zero from `words` up to the next multiple of 4.
 template <int T>
 __device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t s, const uint32_t *bm,
                              uint32_t words, uint32_t v0, uint32_t *stage_all, SharedMisc &m) {
     constexpr int NW = T / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t wpw = ((((words + NW - 1) / NW) + 31u) & ~31u);
+    const uint32_t wpl = a.stage ? 1u : a.wpl;
+    const uint32_t step = 32u * wpl;
+    const uint32_t wpw = (((words + NW - 1) / NW) + step - 1) / step * step;
     const uint32_t w0 = min(words, (uint32_t)warp * wpw), w1 = min(words, w0 + wpw);
 
-    uint32_t cnt = 0;
-    for (uint32_t i = w0 + lane; i < w1; i += 32) cnt += __popc(bm[i]);
-    cnt = warp_sum_u32(cnt);
+    uint32_t cnt;
+    if (wpl == 4) cnt = count_words<4>(bm, w0, w1);
+    else if (wpl == 2) cnt = count_words<2>(bm, w0, w1);
+    else cnt = count_words<1>(bm, w0, w1);
     if (lane == 0) m.wcount[warp] = cnt;
     __syncthreads();
     if (warp == 0) {
@@ -263,29 +349,11 @@ __device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t
     }
     __syncthreads();
 
-    uint32_t *stage = stage_all + warp * kStageWords;
-    uint32_t *out = a.out;
-    const uint64_t lim = a.n;
-    uint64_t base = m.excl + m.wbase[warp];
-    for (uint32_t i0 = w0; i0 < w1; i0 += 32) {
-        const uint32_t i = i0 + lane;
-        uint32_t v = i < w1 ? bm[i] : 0u;
-        const uint32_t c = __popc(v);
-        const uint32_t incl = warp_incl_scan_u32(c, lane);
-        const uint32_t chunk = __shfl_sync(kFull, incl, 31);
-        uint32_t pos = incl - c;
-        const uint32_t val = v0 + i * 32u;
-        while (v) {
-            const uint32_t bit = __ffs(v) - 1;
-            stage[pos++] = val + bit;
-            v &= v - 1;
-        }
-        __syncwarp();
-        for (uint32_t k = lane; k < chunk; k += 32)
-            if (base + k < lim) __stcs(out + base + k, stage[k]);   // never past n, whatever the scratch held
-        base += chunk;
-        __syncwarp();
-    }
+    const uint64_t base = m.excl + m.wbase[warp];
+    if (a.stage) emit_words<1, true>(bm, w0, w1, v0, base, a.out, a.n, stage_all + warp * kStageWords);
+    else if (wpl == 4) emit_words<4, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
+    else if (wpl == 2) emit_words<2, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
+    else emit_words<1, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
 
     // The CTA that finishes the array's last slice writes the outcome and
     // returns the array's scratch to its zero state for the next launch.
@@ -316,14 +384,17 @@ __device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t
 }
 
 // ------------------------------------------------------------------ items
+// Shared part of HIST: add the buckets of p[lo, hi) to the shared histogram
+// (keys above max_value are only reported), then add it to the global counts.
+// Returns true in the CTA that completed the last of `expected` contributions;
+// that CTA then turns the counts into bucket offsets.
 template <int T>
-__device__ void item_hist(const EngineParams &P, const ArrayDesc &a, uint32_t tile, char *smem, SharedMisc &m) {
+__device__ void hist_range(const ArrayDesc &a, uint64_t lo, uint64_t hi, uint32_t expected, char *smem,
+                           SharedMisc &m) {
     const uint32_t nb = a.nslices;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
     for (uint32_t i = threadIdx.x; i < nb; i += T) hist[i] = 0;
     __syncthreads();
-    const uint64_t lo = (uint64_t)tile * a.tile_keys;
-    const uint64_t hi = min(lo + a.tile_keys, a.n);
     bool bad = false;
     const uint64_t M = a.M, magic = a.div_magic;
     for_each_key<T, false>(a.keys, lo, hi, [&](uint32_t x) {
@@ -340,7 +411,7 @@ __device__ void item_hist(const EngineParams &P, const ArrayDesc &a, uint32_t ti
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t d = atomicAdd(&a.sync[SY_HIST_DONE], 1u);
-        m.flag = (d == a.key_tiles - 1) ? 1u : 0u;
+        m.flag = (d == expected - 1) ? 1u : 0u;
     }
     __syncthreads();
     if (m.flag) {
@@ -355,16 +426,26 @@ __device__ void item_hist(const EngineParams &P, const ArrayDesc &a, uint32_t ti
 }
 
 template <int T>
+__device__ void item_hist(const EngineParams &P, const ArrayDesc &a, uint32_t tile, char *smem, SharedMisc &m) {
+    const uint64_t lo = (uint64_t)tile * a.tile_keys;
+    hist_range<T>(a, lo, min(lo + a.tile_keys, a.n), a.key_tiles, smem, m);
+}
+
+template <int T>
 __device__ void item_part(const EngineParams &P, const ArrayDesc &a, uint32_t tile, char *smem, SharedMisc &m) {
     constexpr int K = kKeysPerThread;
     const uint32_t nb = a.nslices;
+    const bool capacity = a.layout == LAYOUT_CAPACITY;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
     uint32_t *lpre = hist + nb;
     uint64_t *gpos = reinterpret_cast<uint64_t *>(lpre + nb);
     uint32_t *sorted = reinterpret_cast<uint32_t *>(gpos + nb);
 
-    if (threadIdx.x == 0)
-        m.flag = wait_geq(&a.sync[SY_OFFSETS_READY], 1u, &a.sync[SY_TIMEOUT], P.wait_limit_ns) ? 1u : 0u;
+    if (threadIdx.x == 0) {
+        m.flag = 1u;
+        if (!capacity && !a.phased)
+            m.flag = wait_geq(&a.sync[SY_OFFSETS_READY], 1u, &a.sync[SY_TIMEOUT], P.wait_limit_ns) ? 1u : 0u;
+    }
     for (uint32_t i = threadIdx.x; i < nb; i += T) hist[i] = 0;
     __syncthreads();
     if (m.flag) {
@@ -404,47 +485,66 @@ __device__ void item_part(const EngineParams &P, const ArrayDesc &a, uint32_t ti
                 }
             }
         }
+        bool bad = false;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             r[j] = 0;
             if ((valid >> j) & 1u) {
                 if ((uint64_t)x[j] < M) r[j] = atomicAdd(&hist[bucket_of(x[j], magic)], 1u);
-                else valid &= ~(1u << j);
+                else {
+                    valid &= ~(1u << j);
+                    bad = true;
+                }
             }
         }
-        __syncthreads();
+        bad = __syncthreads_or(bad);
+        if (bad && threadIdx.x == 0 && capacity) atomicOr(&a.sync[SY_RANGE], 1u);
         const uint64_t total = block_exclusive_scan<T>(
             nb, [&](uint32_t i) -> uint64_t { return hist[i]; },
             [&](uint32_t i, uint64_t v) { lpre[i] = (uint32_t)v; }, m);
+        // reserve each bucket's run in the partition buffer
         for (uint32_t i = threadIdx.x; i < nb; i += T) {
             const uint32_t c = hist[i];
-            if (c) gpos[i] = __ldcg(&a.offsets[i]) + atomicAdd(&a.cursor[i], c);
+            if (c) {
+                const uint64_t at = atomicAdd(&a.cursor[i], c);
+                if (capacity) {
+                    gpos[i] = (uint64_t)i * a.cap + at;
+                    if (at + c > a.cap) atomicOr(&a.sync[SY_OVERFLOW], 1u);   // only with repeated keys
+                } else {
+                    gpos[i] = __ldcg(&a.offsets[i]) + at;
+                }
+            }
         }
 #pragma unroll
         for (int j = 0; j < K; ++j)
             if ((valid >> j) & 1u) sorted[lpre[bucket_of(x[j], magic)] + r[j]] = x[j];
         __syncthreads();
         uint32_t *part = a.part;
-        const uint64_t lim = a.n;
+        const uint64_t cap = a.cap;
+        const uint64_t lim = capacity ? (uint64_t)nb * cap : a.n;
         for (uint32_t i = threadIdx.x; i < (uint32_t)total; i += T) {
             const uint32_t v = sorted[i];
             const uint32_t b = bucket_of(v, magic);
-            const uint64_t dst = gpos[b] + (i - lpre[b]);
-            if (dst < lim) part[dst] = v;
+            const uint64_t rank = gpos[b] + (i - lpre[b]);
+            // CAPACITY: a bucket's run never spills into the next bucket
+            const bool fits = capacity ? rank < (uint64_t)(b + 1) * cap : rank < lim;
+            if (fits) part[rank] = v;
         }
     } else if (threadIdx.x == 0) {
         atomicOr(&a.sync[SY_TIMEOUT], 1u);
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(&a.sync[SY_PART_DONE], 1u);
+    if (!a.phased) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&a.sync[SY_PART_DONE], 1u);
+    }
 }
 
 template <int T>
 __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t b, char *smem, SharedMisc &m) {
     constexpr int NW = T / 32;
     uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *bm = stage + NW * kStageWords;
+    uint32_t *bm = a.stage ? stage + NW * kStageWords : stage;
     const uint64_t v0 = (uint64_t)b * a.S;
     const uint64_t vals = min((uint64_t)a.S, a.M - v0);
     const uint32_t words = (uint32_t)((vals + 31) >> 5);
@@ -453,7 +553,7 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
 
     if (threadIdx.x == 0) {
         m.flag = 1u;
-        if (partitioned)
+        if (partitioned && !a.phased)
             m.flag = wait_geq(&a.sync[SY_PART_DONE], a.key_tiles + a.stall, &a.sync[SY_TIMEOUT], P.wait_limit_ns)
                          ? 1u : 0u;
     }
@@ -462,14 +562,24 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     __syncthreads();
     bool bad = false;
     if (m.flag) {
-        if (partitioned) {
+        const uint32_t base = (uint32_t)v0, span = (uint32_t)vals;
+        auto set_bit = [&](uint32_t x) {
+            const uint32_t l = x - base;
+            if (l < span) atomicOr(&bm[l >> 5], 1u << (l & 31));
+        };
+        if (partitioned && a.layout == LAYOUT_CAPACITY) {
+            const uint64_t filled = __ldcg(&a.cursor[b]);
+            if (filled <= a.cap) {
+                for_each_key<T, true>(a.part, (uint64_t)b * a.cap, (uint64_t)b * a.cap + filled, set_bit);
+            } else {
+                // more keys than the bucket holds: only possible with repeated
+                // keys; take the bucket's keys from the whole input instead
+                for_each_key<T, true>(a.keys, 0, a.n, set_bit);
+            }
+        } else if (partitioned) {
             const uint64_t start = min(__ldcg(&a.offsets[b]), a.n);
             const uint64_t cnt = min((uint64_t)__ldcg(&a.counts[b]), a.n - start);
-            const uint32_t base = (uint32_t)v0, span = (uint32_t)vals;
-            for_each_key<T, true>(a.part, start, start + cnt, [&](uint32_t x) {
-                const uint32_t l = x - base;
-                if (l < span) atomicOr(&bm[l >> 5], 1u << (l & 31));
-            });
+            for_each_key<T, true>(a.part, start, start + cnt, set_bit);
         } else {
             const uint64_t M = a.M;
             for_each_key<T, true>(a.keys, 0, a.n, [&](uint32_t x) {
@@ -489,10 +599,9 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     slice_finish<T>(P, a, b, bm, words, (uint32_t)v0, stage, m);
 }
 
+// GSCATTER: OR the keys of p[lo, hi) into the global bitmap (L2 atomics).
 template <int T>
-__device__ void item_gscatter(const EngineParams &P, const ArrayDesc &a, uint32_t tile, SharedMisc &m) {
-    const uint64_t lo = (uint64_t)tile * a.tile_keys;
-    const uint64_t hi = min(lo + a.tile_keys, a.n);
+__device__ void gscatter_range(const ArrayDesc &a, uint64_t lo, uint64_t hi) {
     const uint64_t M = a.M;
     uint32_t *bitmap = a.bitmap;
     bool bad = false;
@@ -502,6 +611,12 @@ __device__ void item_gscatter(const EngineParams &P, const ArrayDesc &a, uint32_
     });
     bad = __syncthreads_or(bad);
     if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
+}
+
+template <int T>
+__device__ void item_gscatter(const EngineParams &P, const ArrayDesc &a, uint32_t tile, SharedMisc &m) {
+    const uint64_t lo = (uint64_t)tile * a.tile_keys;
+    gscatter_range<T>(a, lo, min(lo + a.tile_keys, a.n));
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(&a.sync[SY_PART_DONE], 1u);
@@ -511,14 +626,17 @@ template <int T>
 __device__ void item_gscan(const EngineParams &P, const ArrayDesc &a, uint32_t s, char *smem, SharedMisc &m) {
     constexpr int NW = T / 32;
     uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *bm = stage + NW * kStageWords;
+    uint32_t *bm = a.stage ? stage + NW * kStageWords : stage;
     const uint64_t v0 = (uint64_t)s * a.S;
     const uint64_t vals = min((uint64_t)a.S, a.M - v0);
     const uint32_t words = (uint32_t)((vals + 31) >> 5);
     const uint32_t w4 = (words + 3u) & ~3u;
-    if (threadIdx.x == 0)
-        m.flag = wait_geq(&a.sync[SY_PART_DONE], a.key_tiles + a.stall, &a.sync[SY_TIMEOUT], P.wait_limit_ns) ? 1u
-                                                                                                              : 0u;
+    if (threadIdx.x == 0) {
+        m.flag = 1u;
+        if (!a.phased)
+            m.flag = wait_geq(&a.sync[SY_PART_DONE], a.key_tiles + a.stall, &a.sync[SY_TIMEOUT], P.wait_limit_ns)
+                         ? 1u : 0u;
+    }
     __syncthreads();
     uint4 *bm4 = reinterpret_cast<uint4 *>(bm);
     uint4 *src = reinterpret_cast<uint4 *>(a.bitmap + (v0 >> 5));
@@ -577,28 +695,137 @@ __global__ void __launch_bounds__(T) engine_kernel(const __grid_constant__ Engin
     }
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the previous kernel of the stream drains;
+// griddepcontrol.wait blocks until that kernel has completed and its writes
+// are visible (a no-op when there is no such dependency).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// One phase of the sort of a single array (P.one) as its own kernel, so that
+// each phase runs with the occupancy its shared memory allows.  Slice phases
+// take their slices in ticket order (the look-back needs it); tile phases use
+// a grid-stride loop.
+template <int T, int TYPE>
+__global__ void __launch_bounds__(T) phase_kernel(const __grid_constant__ EngineParams P) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ SharedMisc m;
+    pdl_wait();
+    const ArrayDesc &a = P.one;
+    if constexpr (TYPE == IT_BUCKET || TYPE == IT_GSCAN) {
+        for (;;) {
+            if (threadIdx.x == 0) m.ticket = atomicAdd(&P.ticket[0], 1u);
+            __syncthreads();
+            const uint32_t t = m.ticket;
+            __syncthreads();
+            if (t >= P.total_items) break;
+            if constexpr (TYPE == IT_BUCKET) item_bucket<T>(P, a, t, smem, m);
+            else item_gscan<T>(P, a, t, smem, m);
+            __syncthreads();
+        }
+        pdl_trigger();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(&P.ticket[1], 1u) == gridDim.x - 1) {
+                P.ticket[0] = 0;
+                P.ticket[1] = 0;
+                __threadfence();
+            }
+        }
+    } else if constexpr (TYPE == IT_PART) {
+        for (uint32_t t = blockIdx.x; t < P.total_items; t += gridDim.x) {
+            item_part<T>(P, a, t, smem, m);
+            __syncthreads();
+        }
+        pdl_trigger();
+    } else {
+        // HIST / GSCATTER stream one contiguous chunk of keys per CTA (one
+        // flush of the shared histogram, one completion count per CTA)
+        const uint64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + 3) & ~3ull;
+        const uint64_t lo = min((uint64_t)blockIdx.x * chunk, a.n);
+        const uint64_t hi = min(lo + chunk, a.n);
+        if constexpr (TYPE == IT_HIST) hist_range<T>(a, lo, hi, gridDim.x, smem, m);
+        else gscatter_range<T>(a, lo, hi);
+        pdl_trigger();
+    }
+}
+
 // ------------------------------------------------------------------- host
+using KernelFn = void (*)(EngineParams);
+
+// kind: -1 = persistent engine, else an ItemType (one phase)
+static KernelFn kernel_for(int kind, int threads) {
+    if (threads == 256) {
+        switch (kind) {
+            case -1: return engine_kernel<256>;
+            case IT_HIST: return phase_kernel<256, IT_HIST>;
+            case IT_PART: return phase_kernel<256, IT_PART>;
+            case IT_BUCKET: return phase_kernel<256, IT_BUCKET>;
+            case IT_GSCATTER: return phase_kernel<256, IT_GSCATTER>;
+            case IT_GSCAN: return phase_kernel<256, IT_GSCAN>;
+        }
+    } else if (threads == 512) {
+        switch (kind) {
+            case -1: return engine_kernel<512>;
+            case IT_HIST: return phase_kernel<512, IT_HIST>;
+            case IT_PART: return phase_kernel<512, IT_PART>;
+            case IT_BUCKET: return phase_kernel<512, IT_BUCKET>;
+            case IT_GSCATTER: return phase_kernel<512, IT_GSCATTER>;
+            case IT_GSCAN: return phase_kernel<512, IT_GSCAN>;
+        }
+    }
+    return nullptr;
+}
+
 int engine_set_smem_limit(int threads, uint32_t smem_bytes) {
-    cudaError_t e;
-    if (threads == 256) e = cudaFuncSetAttribute(engine_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-    else if (threads == 512) e = cudaFuncSetAttribute(engine_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-    else return (int)cudaErrorInvalidValue;
-    return (int)e;
+    for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN}) {
+        KernelFn f = kernel_for(kind, threads);
+        if (!f) return (int)cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        if (e != cudaSuccess) return (int)e;
+    }
+    return 0;
 }
 
 int engine_max_blocks_per_sm(int threads, uint32_t smem_bytes, int *blocks) {
-    cudaError_t e;
-    if (threads == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, engine_kernel<256>, 256, smem_bytes);
-    else if (threads == 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, engine_kernel<512>, 512, smem_bytes);
-    else return (int)cudaErrorInvalidValue;
-    return (int)e;
+    return kernel_max_blocks_per_sm(-1, threads, smem_bytes, blocks);
+}
+
+int kernel_max_blocks_per_sm(int kind, int threads, uint32_t smem_bytes, int *blocks) {
+    KernelFn f = kernel_for(kind, threads);
+    if (!f) return (int)cudaErrorInvalidValue;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem_bytes);
 }
 
 int engine_launch(const EngineParams &p, int threads, uint32_t smem_bytes, int grid, void *stream) {
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (threads == 256) engine_kernel<256><<<grid, 256, smem_bytes, s>>>(p);
-    else if (threads == 512) engine_kernel<512><<<grid, 512, smem_bytes, s>>>(p);
-    else return (int)cudaErrorInvalidValue;
+    return kernel_launch(-1, p, threads, smem_bytes, grid, stream, false);
+}
+
+int kernel_launch(int kind, const EngineParams &p, int threads, uint32_t smem_bytes, int grid, void *stream,
+                  bool pdl) {
+    KernelFn f = kernel_for(kind, threads);
+    if (!f) return (int)cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem_bytes;
+    cfg.stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    if (pdl) {
+        e = cudaLaunchKernelEx(&cfg, f, p);
+        if (e == cudaSuccess) return 0;
+        // a stream or driver that does not take programmatic serialization:
+        // launch in plain stream order instead
+        if (getenv("BITSORT_VERBOSE"))
+            fprintf(stderr, "bitsort: programmatic launch refused (%s); plain launch\n", cudaGetErrorString(e));
+        cudaGetLastError();
+    }
+    f<<<grid, threads, smem_bytes, cfg.stream>>>(p);
     return (int)cudaGetLastError();
 }
 

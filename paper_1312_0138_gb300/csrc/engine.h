@@ -38,6 +38,7 @@ enum SyncSlot : uint32_t {
     SY_RANGE = 3,         // a key above max_value was seen
     SY_TIMEOUT = 4,       // a bounded wait ran out
     SY_SLICES_DONE = 5,   // BUCKET / GSCAN items finished
+    SY_OVERFLOW = 6,      // CAPACITY layout: a bucket got more keys than it can hold
     SY_COUNT = 8
 };
 
@@ -67,7 +68,20 @@ struct __align__(16) ArrayDesc {
     uint32_t key_tiles;         // number of such tiles
     uint32_t path;              // bitsort_path_t
     uint32_t stall;             // extra never-scheduled PART tiles (failure-path test)
+    uint64_t cap;               // CAPACITY layout: partition-buffer entries per bucket
+    uint32_t layout;            // LAYOUT_EXACT or LAYOUT_CAPACITY (PARTITION path)
+    uint32_t wpl;               // bitmap words per lane in the scan (1, 2 or 4)
+    uint32_t stage;             // 1: stage set-bit positions in shared memory per warp
+    uint32_t phased;            // 1: phases are separate kernels (ordered by the stream)
+    uint32_t reserved[2];
 };
+
+// PARTITION-path layouts of the partition buffer.
+//   EXACT     a histogram pass gives every bucket its exact range (prefix of
+//             the counts); n entries in all, the output buffer can hold them.
+//   CAPACITY  bucket b owns entries [b*cap, (b+1)*cap) with cap = min(S, n):
+//             distinct keys never overflow it, so no histogram pass is needed.
+enum Layout : uint32_t { LAYOUT_EXACT = 0, LAYOUT_CAPACITY = 1 };
 
 // A run of `count` consecutive tickets that all belong to one (array, type).
 struct Segment {
@@ -92,10 +106,10 @@ struct EngineParams {
 
 // Shared-memory sizes (bytes) an item type needs for a given configuration.
 constexpr uint32_t kStageWords = 1024;  // per warp: 32 words x 32 bits
-inline uint32_t slice_smem_bytes(uint32_t S, int threads) {
+inline uint32_t slice_smem_bytes(uint32_t S, int threads, bool stage) {
     uint32_t words = (S + 31) / 32;
     uint32_t w4 = (words + 3) & ~3u;
-    return w4 * 4 + (uint32_t)(threads / 32) * kStageWords * 4;
+    return w4 * 4 + (stage ? (uint32_t)(threads / 32) * kStageWords * 4 : 0u);
 }
 inline uint32_t part_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
     return nslices * 16u + tile_keys * 4u;
@@ -109,5 +123,10 @@ constexpr uint32_t kMaxSlices = 8192;
 int engine_launch(const EngineParams &p, int threads, uint32_t smem_bytes, int grid, void *stream);
 int engine_max_blocks_per_sm(int threads, uint32_t smem_bytes, int *blocks);
 int engine_set_smem_limit(int threads, uint32_t smem_bytes);
+// One phase (kind = an ItemType) of a single array, or the persistent engine
+// (kind = -1); pdl = may start while the previous kernel of the stream drains.
+int kernel_launch(int kind, const EngineParams &p, int threads, uint32_t smem_bytes, int grid, void *stream,
+                  bool pdl);
+int kernel_max_blocks_per_sm(int kind, int threads, uint32_t smem_bytes, int *blocks);
 
 }  // namespace bsx

@@ -17,6 +17,10 @@ struct bsx_config {
     bitsort_path_t path = BITSORT_PATH_PARTITION;
     uint32_t S = 1u << 18;   // values per shared-memory slice (multiple of 128)
     int threads = 512;       // block size of the engine kernel
+    bool persistent = false; // all phases in one persistent launch (else one kernel per phase)
+    uint32_t layout = 1;     // PARTITION: bsx::LAYOUT_EXACT (0) or bsx::LAYOUT_CAPACITY (1)
+    uint32_t wpl = 2;        // bitmap words per lane in the scan (1, 2, 4)
+    bool stage = false;      // stage set-bit positions per warp in shared memory
     double ms = 0;           // measured time when tuned (0 = not measured)
 };
 
@@ -52,6 +56,7 @@ struct bitsort_ctx {
 };
 
 bitsort_status_t bsx_check(cudaError_t e);
+void bsx_note_error(int e, const char *where);
 bitsort_ctx *bsx_default_ctx();
 uint64_t bsx_div_magic(uint32_t S);
 bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M);

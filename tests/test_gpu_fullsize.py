@@ -22,11 +22,13 @@ def ctx():
     (1 << 24, 1 << 28, "floyd", 1),       # L2-resident bitmap, 64 MiB of keys
     (1 << 24, 1 << 32, "feistel", 2),     # sparse full 32-bit range
 ])
-@pytest.mark.parametrize("path", [None, bs.PATH_PARTITION, bs.PATH_GLOBAL])
-def test_full_size_exact(ctx, n, M, method, cfg, path):
+@pytest.mark.parametrize("strat", [None, (bs.PATH_PARTITION, 0), (bs.PATH_PARTITION, 1), (bs.PATH_GLOBAL, 0)],
+                         ids=["default", "exact", "capacity", "global"])
+def test_full_size_exact(ctx, n, M, method, cfg, strat):
     keys_np = gen.keys(gen.SEED_BASE + cfg, n, M, method)
+    path = None if strat is None else strat[0]
     if path is not None:
-        ctx.set_config(n, M - 1, path)
+        ctx.set_config(n, M - 1, path, layout=strat[1])
     st, cnt, out = ctx.sort(to_dev(keys_np), M - 1)
     if path is not None:
         ctx.set_config(n, M - 1, bs.PATH_AUTO)

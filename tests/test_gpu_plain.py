@@ -36,25 +36,38 @@ def check(ctx, keys, max_value, **kw):
 SIZES = [(1, 1), (3, 40), (1000, 1 << 12), (4097, 8200), (40_000, 300_007),
          (100_000, 1 << 20), (70_001, 1 << 24), (20_000, 1 << 32), (262_147, 1 << 19)]
 CONFIGS = [
-    ("fused512", bs.PATH_FUSED, 0, 512),
-    ("fused256", bs.PATH_FUSED, 0, 256),
-    ("part_S128", bs.PATH_PARTITION, 128, 512),
-    ("part_S4096_256", bs.PATH_PARTITION, 4096, 256),
-    ("part_S65536", bs.PATH_PARTITION, 1 << 16, 512),
-    ("part_S1M", bs.PATH_PARTITION, 1 << 20, 512),
-    ("part_odd", bs.PATH_PARTITION, 883_072, 512),
-    ("global_S16K", bs.PATH_GLOBAL, 1 << 14, 512),
-    ("global_S1M_256", bs.PATH_GLOBAL, 1 << 20, 256),
+    ("fused512_w1_stage", bs.PATH_FUSED, 0, 512, dict(words_per_lane=1, stage=1)),
+    ("fused256_w4", bs.PATH_FUSED, 0, 256, dict(words_per_lane=4)),
+    ("fused512_w2_persist", bs.PATH_FUSED, 0, 512, dict(words_per_lane=2, persistent=1)),
+    ("exact_S128_w1", bs.PATH_PARTITION, 128, 512, dict(layout=0, words_per_lane=1)),
+    ("cap_S4096_256_w2", bs.PATH_PARTITION, 4096, 256, dict(layout=1, words_per_lane=2)),
+    ("exact_S64K_stage", bs.PATH_PARTITION, 1 << 16, 512, dict(layout=0, stage=1)),
+    ("cap_S1M_w4", bs.PATH_PARTITION, 1 << 20, 512, dict(layout=1, words_per_lane=4)),
+    ("cap_odd_persist", bs.PATH_PARTITION, 883_072, 256, dict(layout=1, persistent=1, words_per_lane=2)),
+    ("exact_odd_persist_stage", bs.PATH_PARTITION, 883_072, 512, dict(layout=0, persistent=1, stage=1)),
+    ("exact_S4096_persist_w4", bs.PATH_PARTITION, 4096, 256, dict(layout=0, persistent=1, words_per_lane=4)),
+    ("global_S16K_w1", bs.PATH_GLOBAL, 1 << 14, 512, dict(words_per_lane=1)),
+    ("global_S1M_256_w4", bs.PATH_GLOBAL, 1 << 20, 256, dict(words_per_lane=4)),
+    ("global_S64K_persist_stage", bs.PATH_GLOBAL, 1 << 16, 256, dict(persistent=1, stage=1)),
 ]
 
 
-@pytest.mark.parametrize("name,path,S,threads", CONFIGS, ids=[c[0] for c in CONFIGS])
+@pytest.mark.parametrize("name,path,S,threads,extra", CONFIGS, ids=[c[0] for c in CONFIGS])
 @pytest.mark.parametrize("n,M", SIZES, ids=[f"n{n}_M{M}" for n, M in SIZES])
-def test_parity_paths(ctx, name, path, S, threads, n, M):
+def test_parity_paths(ctx, name, path, S, threads, extra, n, M):
     if path == bs.PATH_FUSED and M > (1 << 20):
         pytest.skip("fused needs the whole bitmap in one CTA")
     keys = gen.floyd(hash((n, M)) & 0xFFFF, n, M)
-    check(ctx, keys, M - 1, path=path, S=S, threads=threads)
+    check(ctx, keys, M - 1, path=path, S=S, threads=threads, **extra)
+
+
+# the four strategies the error-path tests run through
+STRATS = [
+    ("fused", dict(path=bs.PATH_FUSED)),
+    ("exact", dict(path=bs.PATH_PARTITION, S=4096, layout=0)),
+    ("capacity", dict(path=bs.PATH_PARTITION, S=4096, layout=1)),
+    ("global", dict(path=bs.PATH_GLOBAL, S=4096)),
+]
 
 
 def test_config0_default_path(ctx):
@@ -80,36 +93,49 @@ def test_empty_and_single(ctx):
 
 def test_extremes_full_range(ctx):
     keys = np.array([U32MAX, 0, 1 << 31, (1 << 31) - 1, U32MAX - 1, 12345], np.uint32)
-    for path in (None, bs.PATH_PARTITION, bs.PATH_GLOBAL):
-        check(ctx, keys, U32MAX, path=path)
+    for strat in [dict()] + [st for name, st in STRATS if name != "fused"]:
+        check(ctx, keys, U32MAX, **strat)
 
 
-@pytest.mark.parametrize("path", [bs.PATH_FUSED, bs.PATH_PARTITION, bs.PATH_GLOBAL])
-def test_in_place(ctx, path):
+@pytest.mark.parametrize("name,strat", STRATS, ids=[x[0] for x in STRATS])
+def test_in_place(ctx, name, strat):
     keys = gen.floyd(77, 50_000, 1 << 20)
-    check(ctx, keys, (1 << 20) - 1, path=path, inplace=True)
+    check(ctx, keys, (1 << 20) - 1, inplace=True, **strat)
 
 
-@pytest.mark.parametrize("path", [bs.PATH_FUSED, bs.PATH_PARTITION, bs.PATH_GLOBAL])
+@pytest.mark.parametrize("name,strat", STRATS, ids=[x[0] for x in STRATS])
 @pytest.mark.parametrize("offset", [1, 2, 3])
-def test_unaligned_pointers(ctx, path, offset):
+def test_unaligned_pointers(ctx, name, strat, offset):
     keys = gen.floyd(78 + offset, 33_333, 1 << 20)
-    check(ctx, keys, (1 << 20) - 1, path=path, offset=offset)
+    check(ctx, keys, (1 << 20) - 1, offset=offset, **strat)
 
 
-@pytest.mark.parametrize("path", [bs.PATH_FUSED, bs.PATH_PARTITION, bs.PATH_GLOBAL])
-def test_duplicates_give_distinct_prefix(ctx, path):
+@pytest.mark.parametrize("name,strat", STRATS, ids=[x[0] for x in STRATS])
+def test_duplicates_give_distinct_prefix(ctx, name, strat):
     keys = gen.uniform_with_replacement(5, 60_000, 1 << 16)
-    check(ctx, keys, (1 << 16) - 1, path=path)
+    check(ctx, keys, (1 << 16) - 1, **strat)
     keys = np.array([3, 3, 3, 3], np.uint32)
-    check(ctx, keys, 3, path=path)
+    check(ctx, keys, 3, **strat)
 
 
-@pytest.mark.parametrize("path", [bs.PATH_FUSED, bs.PATH_PARTITION, bs.PATH_GLOBAL])
-def test_key_range_skips_and_reports(ctx, path):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_capacity_overflow_from_repeated_keys(ctx, persistent):
+    # one bucket receives more keys than it can hold (only possible with
+    # repeats): that bucket is rebuilt from the whole input
+    rep = np.full(30_000, 5, np.uint32)
+    rest = gen.floyd(21, 20_000, 1 << 18)
+    keys = gen.shuffle(22, np.concatenate([rep, rest]))
+    check(ctx, keys, (1 << 18) - 1, path=bs.PATH_PARTITION, S=4096, layout=1, persistent=persistent)
+
+
+@pytest.mark.parametrize("name,strat", STRATS, ids=[x[0] for x in STRATS])
+def test_key_range_skips_and_reports(ctx, name, strat):
     keys = gen.floyd(9, 20_000, 1 << 18)
     mv = (1 << 17) + 3   # about half the keys are out of range
-    check(ctx, keys, mv, path=path)
+    if strat["path"] == bs.PATH_FUSED:
+        mv = (1 << 16) + 3
+        keys = gen.floyd(9, 20_000, 1 << 17)
+    check(ctx, keys, mv, **strat)
 
 
 def test_host_errors(ctx):
@@ -146,10 +172,10 @@ def test_device_result_pointer(ctx):
 def test_repeated_calls_keep_scratch_clean(ctx):
     # the scratch is returned to zero by the kernel itself: many calls in a
     # row, alternating paths and sizes, stay exact
-    for i in range(12):
-        n, M = [(5000, 1 << 16), (70_000, 1 << 22), (3, 1 << 32)][i % 3]
-        path = [bs.PATH_PARTITION, bs.PATH_GLOBAL, None][i % 3]
-        check(ctx, gen.floyd(100 + i, n, M), M - 1, path=path)
+    for i in range(16):
+        n, M = [(5000, 1 << 16), (70_000, 1 << 22), (3, 1 << 32), (200_000, 1 << 24)][i % 4]
+        strat = [STRATS[1][1], STRATS[3][1], dict(), STRATS[2][1]][i % 4]
+        check(ctx, gen.floyd(100 + i, n, M), M - 1, **strat)
 
 
 def test_autotune_picks_a_correct_config(ctx, tmp_path):
@@ -158,7 +184,8 @@ def test_autotune_picks_a_correct_config(ctx, tmp_path):
     keys = to_dev(keys_np)
     best = ctx.autotune(keys, (1 << 22) - 1, out=torch.empty_like(keys))
     assert best["path"] in ("fused", "partition", "global") and best["ms"] > 0
-    assert ctx.get_config(1 << 18, (1 << 22) - 1)["path"] == best["path"]
+    got = ctx.get_config(1 << 18, (1 << 22) - 1)
+    assert {k: got[k] for k in got if k != "ms"} == {k: best[k] for k in best if k != "ms"}
     check(ctx, keys_np, (1 << 22) - 1)
     p = str(tmp_path / "tune.json")
     ctx.tune_save(p)
