@@ -218,7 +218,8 @@ def run_plain(args, w, ws, rank, local):
         ctx.autotune(keys, M - 1, out=out)
     if args.path:
         ctx.set_config(n, M - 1, {"fused": 1, "partition": 2, "global": 3}[args.path], args.slice, args.threads,
-                       words_per_lane=args.wpl, stage=args.stage, layout=args.layout, persistent=args.persistent)
+                       words_per_lane=args.wpl, stage=args.stage, layout=args.layout, persistent=args.persistent,
+                       emit=args.emit)
     cfg = ctx.get_config(n, M - 1)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -434,6 +435,7 @@ def main():
     ap.add_argument("--stage", type=int, default=0)
     ap.add_argument("--layout", type=int, default=1)
     ap.add_argument("--persistent", type=int, default=0)
+    ap.add_argument("--emit", type=int, default=0)
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)

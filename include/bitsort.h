@@ -210,6 +210,13 @@ typedef enum {
  *                   bucket in a context buffer, no histogram pass.
  *   persistent      1: all phases in one persistent launch; 0: one kernel
  *                   per phase.
+ *   emit            0 = the lanes walk the set bits of their bitmap words;
+ *                   1 = rank: the per-word popcount prefix is kept next to
+ *                   the bitmap and every key writes itself at its index among
+ *                   the set bits (prefix of its word + popcount of the lower
+ *                   bits), through a shared-memory copy of the slice's output
+ *                   (for sparse bitmaps; falls back to 0 for a slice with
+ *                   more outputs than expected).
  *   ms              measured time when tuned (output only). */
 typedef struct {
     int32_t path;
@@ -219,7 +226,7 @@ typedef struct {
     uint32_t stage;
     uint32_t layout;
     uint32_t persistent;
-    uint32_t reserved;
+    uint32_t emit;
     double ms;
 } bitsort_config_t;
 

@@ -54,17 +54,19 @@ class Result(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("slice_values", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("words_per_lane", ctypes.c_uint32), ("stage", ctypes.c_uint32), ("layout", ctypes.c_uint32),
-                ("persistent", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("ms", ctypes.c_double)]
+                ("persistent", ctypes.c_uint32), ("emit", ctypes.c_uint32), ("ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"path": PATH_NAMES.get(self.path, self.path), "slice_values": self.slice_values,
                 "threads": self.block_threads, "words_per_lane": self.words_per_lane, "stage": self.stage,
                 "layout": LAYOUT_NAMES.get(self.layout, self.layout), "persistent": self.persistent,
-                "ms": self.ms}
+                "emit": EMIT_NAMES.get(self.emit, self.emit), "ms": self.ms}
 
 
 LAYOUT_EXACT, LAYOUT_CAPACITY = 0, 1
 LAYOUT_NAMES = {0: "exact", 1: "capacity"}
+EMIT_WORD, EMIT_RANK = 0, 1
+EMIT_NAMES = {0: "word", 1: "rank"}
 
 
 class Desc(ctypes.Structure):
@@ -210,8 +212,9 @@ class Context:
 
     # tuning ----------------------------------------------------------------
     def set_config(self, n: int, max_value: int, path: int, slice_values: int = 0, threads: int = 0,
-                   words_per_lane: int = 0, stage: int = 0, layout: int = LAYOUT_CAPACITY, persistent: int = 0):
-        cfg = Config(path, slice_values, threads, words_per_lane, stage, layout, persistent, 0, 0.0)
+                   words_per_lane: int = 0, stage: int = 0, layout: int = LAYOUT_CAPACITY, persistent: int = 0,
+                   emit: int = EMIT_WORD):
+        cfg = Config(path, slice_values, threads, words_per_lane, stage, layout, persistent, emit, 0.0)
         _check(load().bitsort_set_config(self.handle, n, max_value, ctypes.byref(cfg)), "bitsort_set_config")
 
     def get_config(self, n: int, max_value: int):

@@ -180,8 +180,16 @@ bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M) {
     }
     cfg.path = BITSORT_PATH_PARTITION;
     cfg.layout = LAYOUT_CAPACITY;
-    // about four slices per SM: four CTAs of 256 threads fit one SM
-    uint64_t target = 4ull * (uint64_t)c->sms;
+    uint64_t target = 4ull * (uint64_t)c->sms;   // four CTAs of 256 threads fit one SM
+    if (n * 8 <= M) {
+        // sparse: rank emission, two CTAs of 512 threads per SM; the slice
+        // takes S/4 bytes (bitmap + prefix) and its staged outputs 5/4 of the
+        // expected 4 n S / M bytes
+        cfg.emit = EMIT_RANK;
+        cfg.threads = 512;
+        const double per_value = 0.25 + 5.0 * (double)n / (double)M;
+        target = std::max<uint64_t>(1, (uint64_t)((double)M * per_value / (double)(c->smem_optin / 2 - 2048)) + 1);
+    }
     uint64_t S = ceil_div(M, target);
     uint64_t lo = std::max<uint64_t>(4096, ceil_div(M, kMaxSlices));
     S = std::max(S, lo);
@@ -220,11 +228,25 @@ bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
         const uint64_t cap = std::min<uint64_t>(cfg.S, n);
         if (nb * cap * 4 > kCapacityScratchMax) cfg.layout = LAYOUT_EXACT;
     }
+    if (cfg.path == BITSORT_PATH_GLOBAL) cfg.emit = EMIT_WORD;   // a global slice has no keys to rank
+    if (cfg.emit != EMIT_WORD && cfg.emit != EMIT_RANK) cfg.emit = EMIT_WORD;
     return cfg;
 }
 
-uint32_t bsx_smem_for(const bsx_config &cfg, uint32_t nslices, uint32_t tile_keys) {
-    uint32_t s = slice_smem_bytes(cfg.S, cfg.threads, cfg.stage);
+// Outputs a slice may stage under EMIT_RANK: 5/4 of the expected count plus
+// a margin (every key lands in one slice: expected = n S / M), at most n.
+uint32_t bsx_stage_cap(const bsx_config &cfg, uint64_t n, uint64_t M) {
+    if (cfg.emit != EMIT_RANK) return 0;
+    if (cfg.path == BITSORT_PATH_FUSED) return (uint32_t)((n + 3) & ~3ull);
+    const double expected = (double)n * (double)cfg.S / (double)M;
+    uint64_t cap = (uint64_t)(expected * 1.25) + 512;
+    cap = std::min<uint64_t>(cap, n);
+    return (uint32_t)((cap + 3) & ~3ull);
+}
+
+uint32_t bsx_smem_for(const bsx_config &cfg, uint32_t nslices, uint32_t tile_keys, uint32_t stage_cap) {
+    uint32_t s = cfg.emit == EMIT_RANK ? rank_smem_bytes(cfg.S, stage_cap)
+                                       : slice_smem_bytes(cfg.S, cfg.threads, cfg.stage);
     if (cfg.path == BITSORT_PATH_PARTITION) {
         s = std::max(s, part_smem_bytes(nslices, tile_keys));
         s = std::max(s, hist_smem_bytes(nslices));
@@ -251,6 +273,8 @@ void bsx_describe(const bsx_config &cfg, const uint32_t *keys, uint32_t *out, ui
     a.phased = cfg.persistent ? 0 : 1;
     a.layout = cfg.path == BITSORT_PATH_PARTITION ? cfg.layout : LAYOUT_EXACT;
     a.cap = a.layout == LAYOUT_CAPACITY ? std::min<uint64_t>(cfg.S, n) : 0;
+    a.emit = cfg.emit;
+    a.stage_cap = bsx_stage_cap(cfg, n, M);
     if (cfg.path == BITSORT_PATH_FUSED) {
         a.nslices = 1;
         a.key_tiles = 0;
@@ -371,7 +395,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     const int T = cfg.threads;
     if (cfg.persistent) {
         // every phase in one persistent launch (items in ticket order)
-        uint32_t smem = bsx_smem_for(cfg, a.nslices, a.tile_keys);
+        uint32_t smem = bsx_smem_for(cfg, a.nslices, a.tile_keys, a.stage_cap);
         if (smem > c->smem_optin) return BITSORT_ERR_INVALID;
         int grid = bsx_grid_for(c, T, smem, p.total_items);
         int e = engine_launch(p, T, smem, grid, stream);
@@ -408,7 +432,8 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         ++launched;
         return true;
     };
-    const uint32_t sl = slice_smem_bytes(cfg.S, T, cfg.stage);
+    const uint32_t sl = cfg.emit == EMIT_RANK ? rank_smem_bytes(cfg.S, a.stage_cap)
+                                              : slice_smem_bytes(cfg.S, T, cfg.stage);
     bool ok = true;
     if (a.path == BITSORT_PATH_FUSED) {
         ok = phase(IT_BUCKET, 1, sl);
@@ -518,7 +543,7 @@ static void to_public(const bsx_config &c, bitsort_config_t *o) {
     o->stage = c.stage ? 1 : 0;
     o->layout = c.layout;
     o->persistent = c.persistent ? 1 : 0;
-    o->reserved = 0;
+    o->emit = c.emit;
     o->ms = c.ms;
 }
 
@@ -542,6 +567,7 @@ extern "C" bitsort_status_t bitsort_set_config(bitsort_ctx_t *c, uint64_t n, uin
     cfg.stage = in->stage != 0;
     cfg.layout = in->layout;
     cfg.persistent = in->persistent != 0;
+    cfg.emit = in->emit;
     c->table[key] = bsx_sanitize(cfg, n, M);
     return BITSORT_OK;
 }
@@ -558,7 +584,8 @@ extern "C" bitsort_status_t bitsort_get_config(bitsort_ctx_t *c, uint64_t n, uin
 // Candidate configurations for (n, M), deduplicated after sanitizing.
 std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_t M) {
     std::vector<bsx_config> out;
-    auto push = [&](bitsort_path_t path, uint64_t S, int threads, uint32_t wpl, bool stage, uint32_t layout) {
+    auto push = [&](bitsort_path_t path, uint64_t S, int threads, uint32_t wpl, bool stage, uint32_t layout,
+                    uint32_t emit = EMIT_WORD) {
         bsx_config cfg;
         cfg.path = path;
         cfg.S = (uint32_t)std::min<uint64_t>(S, 0xFFFFFF80u);
@@ -566,13 +593,28 @@ std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_
         cfg.wpl = wpl;
         cfg.stage = stage;
         cfg.layout = layout;
+        cfg.emit = emit;
         cfg = bsx_sanitize(cfg, n, M);
         for (auto &o : out)
             if (o.path == cfg.path && o.S == cfg.S && o.threads == cfg.threads && o.wpl == cfg.wpl &&
-                o.stage == cfg.stage && o.layout == cfg.layout)
+                o.stage == cfg.stage && o.layout == cfg.layout && o.emit == cfg.emit)
                 return;
         out.push_back(cfg);
     };
+    // rank emission: slices sized for 1 or 2 CTAs per SM
+    for (int threads : {256, 512}) {
+        for (int per_sm : {1, 2, 3}) {
+            const double per_value = 0.25 + 5.0 * (double)n / (double)M;
+            const double budget = (double)(c->smem_optin / per_sm) - 2048.0;
+            if (budget <= 0) continue;
+            const uint64_t S = (uint64_t)(budget / per_value);
+            for (uint32_t layout : {(uint32_t)LAYOUT_EXACT, (uint32_t)LAYOUT_CAPACITY}) {
+                push(BITSORT_PATH_PARTITION, S, threads, 1, false, layout, EMIT_RANK);
+                push(BITSORT_PATH_PARTITION, S / 2, threads, 1, false, layout, EMIT_RANK);
+            }
+        }
+        if (M <= kMaxSliceValues) push(BITSORT_PATH_FUSED, M, threads, 1, false, LAYOUT_EXACT, EMIT_RANK);
+    }
     for (int threads : {256, 512}) {
         for (uint32_t wpl : {1u, 2u, 4u}) {
             if (M <= kMaxSliceValues) push(BITSORT_PATH_FUSED, M, threads, wpl, false, LAYOUT_EXACT);
@@ -600,7 +642,7 @@ std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_
     for (auto &cfg : out) {
         ArrayDesc a;
         bsx_describe(cfg, nullptr, nullptr, n, M, a);
-        if (bsx_smem_for(cfg, a.nslices, a.tile_keys) <= c->smem_optin) fit.push_back(cfg);
+        if (bsx_smem_for(cfg, a.nslices, a.tile_keys, a.stage_cap) <= c->smem_optin) fit.push_back(cfg);
     }
     return fit;
 }
@@ -635,7 +677,7 @@ extern "C" bitsort_status_t bitsort_autotune(bitsort_ctx_t *c, const uint32_t *k
         // one warm-up, then the median of five cold-L2 runs
         ArrayDesc probe;
         bsx_describe(cfg, nullptr, nullptr, n, M, probe);
-        if (bsx_smem_for(cfg, probe.nslices, probe.tile_keys) > c->smem_optin) continue;
+        if (bsx_smem_for(cfg, probe.nslices, probe.tile_keys, probe.stage_cap) > c->smem_optin) continue;
         if (launch_single(c, cfg, keys, n, M, out, nullptr, s, 0) != BITSORT_OK) continue;
         std::vector<float> ts;
         bool ok = true;
@@ -687,9 +729,9 @@ extern "C" bitsort_status_t bitsort_tune_save(bitsort_ctx_t *c, const char *path
         const bsx_config &g = kv.second;
         fprintf(f,
                 "%s\n  {\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
-                "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"ms\": %.6f}",
+                "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"ms\": %.6f}",
                 first ? "" : ",", kv.first.first, kv.first.second, (int)g.path, g.S, g.threads, g.wpl,
-                g.stage ? 1 : 0, g.layout, g.persistent ? 1 : 0, g.ms);
+                g.stage ? 1 : 0, g.layout, g.persistent ? 1 : 0, g.emit, g.ms);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -711,12 +753,12 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
     size_t pos = 0;
     while ((pos = text.find("{\"log2n\"", pos)) != std::string::npos) {
         int ln = 0, lm = 0, p = 0, th = 0, stage = 0, pers = 0;
-        unsigned S = 0, wpl = 0, layout = 0;
+        unsigned S = 0, wpl = 0, layout = 0, emit = 0;
         double ms = 0;
         if (sscanf(text.c_str() + pos,
                    "{\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
-                   "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"ms\": %lf",
-                   &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &ms) != 10)
+                   "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"ms\": %lf",
+                   &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &emit, &ms) != 11)
             return BITSORT_ERR_INVALID;
         if (p < 1 || p > 3 || (th != 256 && th != 512) || ln < 0 || ln > 64 || lm < 0 || lm > 33)
             return BITSORT_ERR_INVALID;
@@ -728,6 +770,7 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
         cfg.stage = stage != 0;
         cfg.layout = layout;
         cfg.persistent = pers != 0;
+        cfg.emit = emit;
         cfg.ms = ms;
         table[std::make_pair(ln, lm)] = cfg;
         ++pos;

@@ -59,6 +59,13 @@ struct bitsort_batch_plan {
 static bsx_config batch_config(bitsort_ctx *c, uint64_t n, uint64_t M, int threads) {
     bsx_config cfg;
     cfg.threads = threads;
+    // one persistent launch: every item waits for its own array's earlier
+    // phases; exact bucket ranges, so the partition buffer is the output (or
+    // an n-entry plan buffer when sorting in place)
+    cfg.persistent = true;
+    cfg.layout = LAYOUT_EXACT;
+    cfg.wpl = 1;
+    cfg.stage = false;
     if (n == 0) {
         cfg.path = BITSORT_PATH_FUSED;
         cfg.S = 128;
@@ -70,7 +77,10 @@ static bsx_config batch_config(bitsort_ctx *c, uint64_t n, uint64_t M, int threa
         cfg.path = BITSORT_PATH_PARTITION;
         cfg.S = 1u << 20;
     }
-    return bsx_sanitize(cfg, n, M);
+    cfg = bsx_sanitize(cfg, n, M);
+    cfg.persistent = true;
+    cfg.layout = LAYOUT_EXACT;
+    return cfg;
 }
 
 bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, size_t count,
@@ -102,7 +112,11 @@ bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, siz
         bsx_config cfg = batch_config(c, n, M, T);
         pl->cfg[i] = cfg;
         bsx_describe(cfg, descs[i].keys, descs[i].out, n, M, arr[i]);
-        smem = std::max(smem, bsx_smem_for(cfg, arr[i].nslices, arr[i].tile_keys));
+        if (arr[i].phased || arr[i].layout != LAYOUT_EXACT) {  // the buffers below are sized for this
+            delete pl;
+            return BITSORT_ERR_INVALID;
+        }
+        smem = std::max(smem, bsx_smem_for(cfg, arr[i].nslices, arr[i].tile_keys, arr[i].stage_cap));
         scr_off[i] = scr;
         size_t need = SY_COUNT * 4;
         if (arr[i].nslices > 1) need += (size_t)arr[i].nslices * 8;                  // look-back

@@ -51,8 +51,13 @@ __device__ __forceinline__ uint64_t now_ns() {
     return t;
 }
 
+// floor(x / S) = floor(x * magic / 2^64) with magic = ceil(2^64 / S).  For a
+// 32-bit x the low half of the magic only contributes the high word of
+// x * lo, a whole number (the fraction below it cannot carry): three integer
+// instructions instead of a 64 x 64 multiply.
 __device__ __forceinline__ uint32_t bucket_of(uint32_t x, uint64_t magic) {
-    return (uint32_t)__umul64hi((uint64_t)x, magic);
+    const uint64_t t = (uint64_t)x * (uint32_t)(magic >> 32) + __umulhi(x, (uint32_t)magic);
+    return (uint32_t)(t >> 32);
 }
 
 __device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
@@ -139,6 +144,37 @@ __device__ uint64_t block_exclusive_scan(uint32_t nb, Load load, Store store, Sh
         run += c;
     }
     const uint64_t total = m.wsum[32];
+    __syncthreads();
+    return total;
+}
+
+// Exclusive prefix sums of the 32-bit counts c[0..nb) written to e[0..nb),
+// in place allowed (e == c); returns the total.  Every thread must call it.
+template <int T>
+__device__ uint32_t block_exclusive_scan_u32(uint32_t nb, const uint32_t *c, uint32_t *e, SharedMisc &m) {
+    constexpr int NW = T / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (nb + T - 1) / T;
+    const uint32_t lo = min(nb, threadIdx.x * per), hi = min(nb, lo + per);
+    uint32_t s = 0;
+    for (uint32_t i = lo; i < hi; ++i) s += c[i];
+    const uint32_t incl = warp_incl_scan_u32(s, lane);
+    if (lane == 31) m.wcount[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < NW ? m.wcount[lane] : 0;
+        const uint32_t wi = warp_incl_scan_u32(w, lane);
+        if (lane < NW) m.wbase[lane] = wi - w;
+        if (lane == 31) m.total = wi;
+    }
+    __syncthreads();
+    uint32_t run = m.wbase[warp] + incl - s;
+    for (uint32_t i = lo; i < hi; ++i) {
+        const uint32_t v = c[i];
+        e[i] = run;
+        run += v;
+    }
+    const uint32_t total = m.total;
     __syncthreads();
     return total;
 }
@@ -281,6 +317,17 @@ __device__ __forceinline__ void emit_words(const uint32_t *bm, uint32_t w0, uint
             for (uint32_t k = lane; k < chunk; k += 32)
                 if (base + k < lim) __stcs(out + base + k, stage[k]);   // never past n, whatever the scratch held
             __syncwarp();
+        } else if (base + chunk <= lim) {   // warp-uniform: the whole step lies inside out[0, n)
+            uint32_t *d = out + base + pos;
+#pragma unroll
+            for (int k = 0; k < WPL; ++k) {
+                const uint32_t val = v0 + (i + k) * 32u - 1u;
+                uint32_t x = v[k];
+                while (x) {
+                    __stcs(d++, val + __ffs(x));
+                    x &= x - 1;
+                }
+            }
         } else {
             uint64_t o = base + pos;
 #pragma unroll
@@ -288,7 +335,7 @@ __device__ __forceinline__ void emit_words(const uint32_t *bm, uint32_t w0, uint
                 const uint32_t val = v0 + (i + k) * 32u;
                 uint32_t x = v[k];
                 while (x) {
-                    if (o < lim) __stcs(out + o, val + (__ffs(x) - 1));
+                    if (o < lim) __stcs(out + o, val + (__ffs(x) - 1));   // never past n
                     ++o;
                     x &= x - 1;
                 }
@@ -316,19 +363,20 @@ __device__ __forceinline__ uint32_t count_words(const uint32_t *bm, uint32_t w0,
     return warp_sum_u32(c);
 }
 
-// Count, look back and write out one bitmap slice held in shared memory.
-// `bm` holds `words` words covering the values v0 .. v0 + 32*words - 1 and is
-// zero from `words` up to the next multiple of 4.
+// Count the set bits of one slice (per warp range, then the block), get the
+// number of set bits of all earlier slices by look-back, and leave in shared
+// memory: m.excl (first output index of the slice), m.total (its set bits),
+// m.wbase[w] (set bits before warp w's range).  Returns the warp's range.
 template <int T>
-__device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t s, const uint32_t *bm,
-                             uint32_t words, uint32_t v0, uint32_t *stage_all, SharedMisc &m) {
+__device__ void slice_count(const EngineParams &P, const ArrayDesc &a, uint32_t s, const uint32_t *bm,
+                            uint32_t words, uint32_t wpl, uint32_t &w0, uint32_t &w1, SharedMisc &m,
+                            bool with_lookback = true) {
     constexpr int NW = T / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t wpl = a.stage ? 1u : a.wpl;
     const uint32_t step = 32u * wpl;
     const uint32_t wpw = (((words + NW - 1) / NW) + step - 1) / step * step;
-    const uint32_t w0 = min(words, (uint32_t)warp * wpw), w1 = min(words, w0 + wpw);
-
+    w0 = min(words, (uint32_t)warp * wpw);
+    w1 = min(words, w0 + wpw);
     uint32_t cnt;
     if (wpl == 4) cnt = count_words<4>(bm, w0, w1);
     else if (wpl == 2) cnt = count_words<2>(bm, w0, w1);
@@ -341,22 +389,29 @@ __device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t
         if (lane < NW) m.wbase[lane] = incl - c;
         const uint32_t total = __shfl_sync(kFull, incl, 31);
         uint64_t excl = 0;
-        if (a.nslices > 1) excl = lookback(P, a, s, total, lane);
+        if (with_lookback && a.nslices > 1) excl = lookback(P, a, s, total, lane);
         if (lane == 0) {
             m.excl = excl;
             m.total = total;
         }
     }
     __syncthreads();
+}
 
-    const uint64_t base = m.excl + m.wbase[warp];
-    if (a.stage) emit_words<1, true>(bm, w0, w1, v0, base, a.out, a.n, stage_all + warp * kStageWords);
-    else if (wpl == 4) emit_words<4, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
-    else if (wpl == 2) emit_words<2, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
-    else emit_words<1, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
+// Look-back of slice s alone (its own count already in m.total).
+template <int T>
+__device__ void slice_lookback(const EngineParams &P, const ArrayDesc &a, uint32_t s, SharedMisc &m) {
+    if (threadIdx.x < 32) {
+        const uint64_t excl = a.nslices > 1 ? lookback(P, a, s, m.total, threadIdx.x) : 0;
+        if (threadIdx.x == 0) m.excl = excl;
+    }
+    __syncthreads();
+}
 
-    // The CTA that finishes the array's last slice writes the outcome and
-    // returns the array's scratch to its zero state for the next launch.
+// The CTA that finishes the array's last slice writes the outcome and
+// returns the array's scratch to its zero state for the next launch.
+template <int T>
+__device__ void slice_complete(const ArrayDesc &a, SharedMisc &m) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -381,6 +436,25 @@ __device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t
             for (int k = 0; k < SY_COUNT; ++k) a.sync[k] = 0;
         }
     }
+}
+
+// Count, look back and write out one bitmap slice held in shared memory by
+// walking its words (EMIT_WORD).  `bm` holds `words` words covering the
+// values v0 .. v0 + 32*words - 1 and is zero from `words` up to the next
+// multiple of 4.
+template <int T>
+__device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t s, const uint32_t *bm,
+                             uint32_t words, uint32_t v0, uint32_t *stage_all, SharedMisc &m) {
+    const int warp = threadIdx.x >> 5;
+    const uint32_t wpl = a.stage ? 1u : a.wpl;
+    uint32_t w0, w1;
+    slice_count<T>(P, a, s, bm, words, wpl, w0, w1, m);
+    const uint64_t base = m.excl + m.wbase[warp];
+    if (a.stage) emit_words<1, true>(bm, w0, w1, v0, base, a.out, a.n, stage_all + warp * kStageWords);
+    else if (wpl == 4) emit_words<4, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
+    else if (wpl == 2) emit_words<2, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
+    else emit_words<1, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
+    slice_complete<T>(a, m);
 }
 
 // ------------------------------------------------------------------ items
@@ -431,107 +505,123 @@ __device__ void item_hist(const EngineParams &P, const ArrayDesc &a, uint32_t ti
     hist_range<T>(a, lo, min(lo + a.tile_keys, a.n), a.key_tiles, smem, m);
 }
 
+// PART: move the keys of one tile to their buckets' runs of the partition
+// buffer.  Every key's bucket and rank inside the tile come from one shared
+// atomic; the tile is then reordered by bucket in shared memory so that each
+// bucket's run leaves in consecutive stores.  Keys above max_value go to an
+// extra discard bin (index nslices) that is never written.  Positions are
+// 32-bit (the buffer has at most 2^32 entries): run start minus the tile-local
+// prefix is kept per bin (delta), so a key's position is delta[b] + its index
+// in the reordered tile; lim[b] ends the part of the run that fits.
 template <int T>
 __device__ void item_part(const EngineParams &P, const ArrayDesc &a, uint32_t tile, char *smem, SharedMisc &m) {
     constexpr int K = kKeysPerThread;
     const uint32_t nb = a.nslices;
+    const uint32_t nbins = nb + 1;
     const bool capacity = a.layout == LAYOUT_CAPACITY;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *lpre = hist + nb;
-    uint64_t *gpos = reinterpret_cast<uint64_t *>(lpre + nb);
-    uint32_t *sorted = reinterpret_cast<uint32_t *>(gpos + nb);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);   // counts, then the tile-local exclusive prefix
+    uint32_t *delta = hist + nbins;
+    uint32_t *lim = delta + nbins;
+    uint32_t *sorted = lim + nbins;
+    uint16_t *sorted_b = reinterpret_cast<uint16_t *>(sorted + a.tile_keys);
 
     if (threadIdx.x == 0) {
         m.flag = 1u;
         if (!capacity && !a.phased)
             m.flag = wait_geq(&a.sync[SY_OFFSETS_READY], 1u, &a.sync[SY_TIMEOUT], P.wait_limit_ns) ? 1u : 0u;
     }
-    for (uint32_t i = threadIdx.x; i < nb; i += T) hist[i] = 0;
+    for (uint32_t i = threadIdx.x; i < nbins; i += T) hist[i] = 0;
     __syncthreads();
-    if (m.flag) {
+    if (!m.flag) {
+        if (threadIdx.x == 0) atomicOr(&a.sync[SY_TIMEOUT], 1u);
+    } else {
         const uint64_t lo = (uint64_t)tile * a.tile_keys;
         const uint64_t hi = min(lo + a.tile_keys, a.n);
-        const uint64_t M = a.M, magic = a.div_magic;
-        uint32_t x[K], r[K];
-        uint32_t valid = 0;
-        const bool vec = (reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0;
-        if (vec) {
+        const uint32_t nkeys = (uint32_t)(hi - lo);
+        const uint64_t magic = a.div_magic;
+        const uint32_t maxv = (uint32_t)(a.M - 1);
+        uint32_t x[K], br[K];   // key; bin << 16 | rank in the tile
+        bool bad = false;
+        if (nkeys == (uint32_t)a.tile_keys && (reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0) {
+            // full tile: K keys per thread, 128-bit loads, no per-key checks
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.keys + lo);
 #pragma unroll
             for (int j = 0; j < K / 4; ++j) {
-                const uint64_t e = lo + (((uint64_t)j * T + threadIdx.x) << 2);
-                if (e + 4 <= hi) {
-                    const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(a.keys + e));
-                    x[4 * j] = q.x; x[4 * j + 1] = q.y; x[4 * j + 2] = q.z; x[4 * j + 3] = q.w;
-                    valid |= 0xFu << (4 * j);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        x[4 * j + k] = 0;
-                        if (e + k < hi) {
-                            x[4 * j + k] = __ldcs(a.keys + e + k);
-                            valid |= 1u << (4 * j + k);
-                        }
-                    }
-                }
+                const uint4 q = __ldcs(src + j * T + threadIdx.x);
+                x[4 * j] = q.x; x[4 * j + 1] = q.y; x[4 * j + 2] = q.z; x[4 * j + 3] = q.w;
             }
-        } else {
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                const uint64_t e = lo + (uint64_t)j * T + threadIdx.x;
+                const bool in = x[j] <= maxv;
+                bad |= !in;
+                const uint32_t bin = in ? bucket_of(x[j], magic) : nb;
+                br[j] = (bin << 16) | atomicAdd(&hist[bin], 1u);
+            }
+        } else {
+            // tail tile or unaligned keys: element-wise, index j*T + tid
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const uint32_t e = (uint32_t)j * T + threadIdx.x;
+                br[j] = 0xFFFFFFFFu;
                 x[j] = 0;
-                if (e < hi) {
-                    x[j] = __ldcs(a.keys + e);
-                    valid |= 1u << j;
+                if (e < nkeys) {
+                    x[j] = __ldcs(a.keys + lo + e);
+                    const bool in = x[j] <= maxv;
+                    bad |= !in;
+                    const uint32_t bin = in ? bucket_of(x[j], magic) : nb;
+                    br[j] = (bin << 16) | atomicAdd(&hist[bin], 1u);
                 }
             }
         }
-        bool bad = false;
+        if (capacity) {
+            bad = __syncthreads_or(bad);
+            if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
+        } else {
+            __syncthreads();   // (the histogram pass reports keys above max_value)
+        }
+        // reserve each bucket's run (needs the counts), then turn counts into prefixes
+        for (uint32_t i = threadIdx.x; i < nbins; i += T) {
+            const uint32_t c = hist[i];
+            uint32_t start = 0, fit = 0;
+            if (c && i < nb) {
+                const uint32_t at = atomicAdd(&a.cursor[i], c);
+                if (capacity) {
+                    const uint64_t cap = a.cap;
+                    start = (uint32_t)((uint64_t)i * cap + at);
+                    fit = at >= cap ? 0u : (uint32_t)min((uint64_t)c, cap - at);
+                    if (fit < c) atomicOr(&a.sync[SY_OVERFLOW], 1u);   // only with repeated keys
+                } else {
+                    const uint64_t st = __ldcg(&a.offsets[i]) + at;
+                    start = (uint32_t)st;
+                    fit = st >= a.n ? 0u : (uint32_t)min((uint64_t)c, a.n - st);   // a sane scratch never clips
+                }
+            }
+            delta[i] = start;
+            lim[i] = fit;
+        }
+        block_exclusive_scan_u32<T>(nbins, hist, hist, m);
+        for (uint32_t i = threadIdx.x; i < nbins; i += T) {
+            const uint32_t p = hist[i];
+            delta[i] -= p;   // position = delta + index in the reordered tile (mod 2^32)
+            lim[i] += p;
+        }
+        __syncthreads();
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            r[j] = 0;
-            if ((valid >> j) & 1u) {
-                if ((uint64_t)x[j] < M) r[j] = atomicAdd(&hist[bucket_of(x[j], magic)], 1u);
-                else {
-                    valid &= ~(1u << j);
-                    bad = true;
-                }
+            if (br[j] != 0xFFFFFFFFu) {
+                const uint32_t bin = br[j] >> 16;
+                const uint32_t at = hist[bin] + (br[j] & 0xFFFFu);
+                sorted[at] = x[j];
+                sorted_b[at] = (uint16_t)bin;
             }
         }
-        bad = __syncthreads_or(bad);
-        if (bad && threadIdx.x == 0 && capacity) atomicOr(&a.sync[SY_RANGE], 1u);
-        const uint64_t total = block_exclusive_scan<T>(
-            nb, [&](uint32_t i) -> uint64_t { return hist[i]; },
-            [&](uint32_t i, uint64_t v) { lpre[i] = (uint32_t)v; }, m);
-        // reserve each bucket's run in the partition buffer
-        for (uint32_t i = threadIdx.x; i < nb; i += T) {
-            const uint32_t c = hist[i];
-            if (c) {
-                const uint64_t at = atomicAdd(&a.cursor[i], c);
-                if (capacity) {
-                    gpos[i] = (uint64_t)i * a.cap + at;
-                    if (at + c > a.cap) atomicOr(&a.sync[SY_OVERFLOW], 1u);   // only with repeated keys
-                } else {
-                    gpos[i] = __ldcg(&a.offsets[i]) + at;
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if ((valid >> j) & 1u) sorted[lpre[bucket_of(x[j], magic)] + r[j]] = x[j];
         __syncthreads();
         uint32_t *part = a.part;
-        const uint64_t cap = a.cap;
-        const uint64_t lim = capacity ? (uint64_t)nb * cap : a.n;
-        for (uint32_t i = threadIdx.x; i < (uint32_t)total; i += T) {
-            const uint32_t v = sorted[i];
-            const uint32_t b = bucket_of(v, magic);
-            const uint64_t rank = gpos[b] + (i - lpre[b]);
-            // CAPACITY: a bucket's run never spills into the next bucket
-            const bool fits = capacity ? rank < (uint64_t)(b + 1) * cap : rank < lim;
-            if (fits) part[rank] = v;
+#pragma unroll 4
+        for (uint32_t i = threadIdx.x; i < nkeys; i += T) {
+            const uint32_t bin = sorted_b[i];
+            if (i < lim[bin]) part[delta[bin] + i] = sorted[i];
         }
-    } else if (threadIdx.x == 0) {
-        atomicOr(&a.sync[SY_TIMEOUT], 1u);
     }
     if (!a.phased) {
         __threadfence();
@@ -543,12 +633,16 @@ __device__ void item_part(const EngineParams &P, const ArrayDesc &a, uint32_t ti
 template <int T>
 __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t b, char *smem, SharedMisc &m) {
     constexpr int NW = T / 32;
-    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *bm = a.stage ? stage + NW * kStageWords : stage;
+    const bool rank = a.emit == EMIT_RANK;
     const uint64_t v0 = (uint64_t)b * a.S;
     const uint64_t vals = min((uint64_t)a.S, a.M - v0);
     const uint32_t words = (uint32_t)((vals + 31) >> 5);
     const uint32_t w4 = (words + 3u) & ~3u;
+    // shared memory: EMIT_WORD [stage (optional) | bitmap]; EMIT_RANK [bitmap | prefix | outputs]
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *bm = (!rank && a.stage) ? stage + NW * kStageWords : stage;
+    uint32_t *pre = bm + w4;
+    uint32_t *outs = pre + w4;
     const bool partitioned = a.path == BITSORT_PATH_PARTITION;
 
     if (threadIdx.x == 0) {
@@ -560,31 +654,37 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     uint4 *bm4 = reinterpret_cast<uint4 *>(bm);
     for (uint32_t i = threadIdx.x; i < w4 / 4; i += T) bm4[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
+
+    // where the slice's keys are: a range of the partition buffer, or the
+    // whole input (fused path, or a capacity bucket that overflowed)
+    const uint32_t *src = a.keys;
+    uint64_t lo = 0, hi = a.n;
+    bool filter_range = !partitioned;   // input keys above max_value are skipped and reported
+    if (partitioned && a.layout == LAYOUT_CAPACITY) {
+        const uint64_t filled = __ldcg(&a.cursor[b]);
+        if (filled <= a.cap) {
+            src = a.part;
+            lo = (uint64_t)b * a.cap;
+            hi = lo + filled;
+        }
+    } else if (partitioned) {
+        src = a.part;
+        lo = min(__ldcg(&a.offsets[b]), a.n);
+        hi = lo + min((uint64_t)__ldcg(&a.counts[b]), a.n - lo);
+    }
+    const uint32_t base = (uint32_t)v0, span = (uint32_t)vals;
     bool bad = false;
     if (m.flag) {
-        const uint32_t base = (uint32_t)v0, span = (uint32_t)vals;
-        auto set_bit = [&](uint32_t x) {
-            const uint32_t l = x - base;
-            if (l < span) atomicOr(&bm[l >> 5], 1u << (l & 31));
-        };
-        if (partitioned && a.layout == LAYOUT_CAPACITY) {
-            const uint64_t filled = __ldcg(&a.cursor[b]);
-            if (filled <= a.cap) {
-                for_each_key<T, true>(a.part, (uint64_t)b * a.cap, (uint64_t)b * a.cap + filled, set_bit);
-            } else {
-                // more keys than the bucket holds: only possible with repeated
-                // keys; take the bucket's keys from the whole input instead
-                for_each_key<T, true>(a.keys, 0, a.n, set_bit);
-            }
-        } else if (partitioned) {
-            const uint64_t start = min(__ldcg(&a.offsets[b]), a.n);
-            const uint64_t cnt = min((uint64_t)__ldcg(&a.counts[b]), a.n - start);
-            for_each_key<T, true>(a.part, start, start + cnt, set_bit);
-        } else {
+        if (filter_range) {
             const uint64_t M = a.M;
-            for_each_key<T, true>(a.keys, 0, a.n, [&](uint32_t x) {
+            for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
                 if ((uint64_t)x < M) atomicOr(&bm[x >> 5], 1u << (x & 31));
                 else bad = true;
+            });
+        } else {
+            for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
+                const uint32_t l = x - base;
+                if (l < span) atomicOr(&bm[l >> 5], 1u << (l & 31));
             });
         }
     } else if (threadIdx.x == 0) {
@@ -596,7 +696,65 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
         a.counts[b] = 0;
         a.cursor[b] = 0;
     }
-    slice_finish<T>(P, a, b, bm, words, (uint32_t)v0, stage, m);
+    if (!rank) {
+        slice_finish<T>(P, a, b, bm, words, (uint32_t)v0, stage, m);
+        return;
+    }
+
+    // EMIT_RANK.  The slice reads its keys a second time below, so it must
+    // not announce its count to later slices before that: a later slice that
+    // knows its output offset may already be writing the output buffer, which
+    // can hold this slice's keys (exact layout).  Ranks inside the slice need
+    // no global offset, so the look-back comes after the second read.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t w0, w1;
+    slice_count<T>(P, a, b, bm, words, 1, w0, w1, m, false);
+    const uint32_t total = m.total;
+    if (total > a.stage_cap) {
+        // more outputs than the staging room (skewed keys): walk the words instead
+        slice_lookback<T>(P, a, b, m);
+        emit_words<1, false>(bm, w0, w1, (uint32_t)v0, m.excl + m.wbase[warp], a.out, a.n, nullptr);
+        slice_complete<T>(a, m);
+        return;
+    }
+    {   // exclusive prefix of the set bits before every word of the slice
+        uint32_t run = m.wbase[warp];
+        for (uint32_t i0 = w0; i0 < w1; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const uint32_t c = i < w1 ? __popc(bm[i]) : 0u;
+            const uint32_t incl = warp_incl_scan_u32(c, lane);
+            if (i < w1) pre[i] = run + incl - c;
+            run += __shfl_sync(kFull, incl, 31);
+        }
+    }
+    __syncthreads();
+    // every key writes itself at its index among the set bits
+    if (filter_range) {
+        const uint64_t M = a.M;
+        for_each_key<T, true>(src, lo, hi, [&](uint32_t x) {
+            if ((uint64_t)x < M) {
+                const uint32_t w = x >> 5;
+                outs[pre[w] + __popc(bm[w] & ((1u << (x & 31)) - 1u))] = x;
+            }
+        });
+    } else {
+        for_each_key<T, true>(src, lo, hi, [&](uint32_t x) {
+            const uint32_t l = x - base;
+            if (l < span) {
+                const uint32_t w = l >> 5;
+                outs[pre[w] + __popc(bm[w] & ((1u << (l & 31)) - 1u))] = x;
+            }
+        });
+    }
+    __syncthreads();
+    slice_lookback<T>(P, a, b, m);
+    {   // the slice's outputs leave in consecutive stores
+        uint32_t *out = a.out;
+        const uint64_t o = m.excl;
+        const uint32_t cnt = (o + total <= a.n) ? total : (o < a.n ? (uint32_t)(a.n - o) : 0u);
+        for (uint32_t i = threadIdx.x; i < cnt; i += T) __stcs(out + o + i, outs[i]);
+    }
+    slice_complete<T>(a, m);
 }
 
 // GSCATTER: OR the keys of p[lo, hi) into the global bitmap (L2 atomics).
@@ -656,7 +814,7 @@ __device__ void item_gscan(const EngineParams &P, const ArrayDesc &a, uint32_t s
 
 // ----------------------------------------------------------------- kernel
 template <int T>
-__global__ void __launch_bounds__(T) engine_kernel(const __grid_constant__ EngineParams P) {
+__global__ void __launch_bounds__(T, 1024 / T) engine_kernel(const __grid_constant__ EngineParams P) {
     extern __shared__ __align__(16) char smem[];
     __shared__ SharedMisc m;
     const Segment *segs = P.segments ? P.segments : P.seg;
@@ -706,8 +864,9 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // each phase runs with the occupancy its shared memory allows.  Slice phases
 // take their slices in ticket order (the look-back needs it); tile phases use
 // a grid-stride loop.
+// at most 64 registers per thread: 1024 threads (four CTAs of 256) fit one SM
 template <int T, int TYPE>
-__global__ void __launch_bounds__(T) phase_kernel(const __grid_constant__ EngineParams P) {
+__global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constant__ EngineParams P) {
     extern __shared__ __align__(16) char smem[];
     __shared__ SharedMisc m;
     pdl_wait();

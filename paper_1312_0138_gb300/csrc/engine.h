@@ -73,8 +73,22 @@ struct __align__(16) ArrayDesc {
     uint32_t wpl;               // bitmap words per lane in the scan (1, 2 or 4)
     uint32_t stage;             // 1: stage set-bit positions in shared memory per warp
     uint32_t phased;            // 1: phases are separate kernels (ordered by the stream)
-    uint32_t reserved[2];
+    uint32_t emit;              // EMIT_WORD or EMIT_RANK (BUCKET items)
+    uint32_t stage_cap;         // EMIT_RANK: outputs a slice may stage in shared memory
 };
+
+// How a BUCKET item turns its bitmap slice into output positions.
+//   EMIT_WORD  every lane walks the set bits of its words (ascending) and
+//              writes their positions; the lanes' counts are prefix-summed.
+//   EMIT_RANK  the exclusive popcount prefix of every word is stored next to
+//              the bitmap; each key x then finds its own index,
+//              prefix[x/32] + popcount of the bits of word x/32 below x, and
+//              is written there in a shared-memory copy of the slice's output,
+//              which leaves in coalesced stores.  Same result: the set bits
+//              in index order.  Needs the slice's keys twice and room for the
+//              slice's outputs; a slice with more outputs than stage_cap falls
+//              back to EMIT_WORD.
+enum Emit : uint32_t { EMIT_WORD = 0, EMIT_RANK = 1 };
 
 // PARTITION-path layouts of the partition buffer.
 //   EXACT     a histogram pass gives every bucket its exact range (prefix of
@@ -111,13 +125,20 @@ inline uint32_t slice_smem_bytes(uint32_t S, int threads, bool stage) {
     uint32_t w4 = (words + 3) & ~3u;
     return w4 * 4 + (stage ? (uint32_t)(threads / 32) * kStageWords * 4 : 0u);
 }
+// EMIT_RANK: bitmap + per-word prefix + staged outputs
+inline uint32_t rank_smem_bytes(uint32_t S, uint32_t stage_cap) {
+    uint32_t words = (S + 31) / 32;
+    uint32_t w4 = (words + 3) & ~3u;
+    return w4 * 8 + ((stage_cap + 3) & ~3u) * 4;
+}
+// PART: per bucket (plus one discard bin) count, delta, limit; the tile and its bucket tags
 inline uint32_t part_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
-    return nslices * 16u + tile_keys * 4u;
+    return (nslices + 1) * 12u + tile_keys * 6u + 16u;
 }
 inline uint32_t hist_smem_bytes(uint32_t nslices) { return nslices * 4u; }
 
 constexpr int kKeysPerThread = 16;   // keys per thread in one HIST/PART/GSCATTER tile
-constexpr uint32_t kMaxSlices = 8192;
+constexpr uint32_t kMaxSlices = 8192;   // bucket ids fit 16 bits in the partition tile
 
 // Host-side launch entry points (engine.cu).
 int engine_launch(const EngineParams &p, int threads, uint32_t smem_bytes, int grid, void *stream);

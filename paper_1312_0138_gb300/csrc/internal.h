@@ -21,6 +21,7 @@ struct bsx_config {
     uint32_t layout = 1;     // PARTITION: bsx::LAYOUT_EXACT (0) or bsx::LAYOUT_CAPACITY (1)
     uint32_t wpl = 2;        // bitmap words per lane in the scan (1, 2, 4)
     bool stage = false;      // stage set-bit positions per warp in shared memory
+    uint32_t emit = 0;       // bsx::EMIT_WORD (0) or bsx::EMIT_RANK (1)
     double ms = 0;           // measured time when tuned (0 = not measured)
 };
 
@@ -62,7 +63,8 @@ uint64_t bsx_div_magic(uint32_t S);
 bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M);
 bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M);
 bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M);
-uint32_t bsx_smem_for(const bsx_config &cfg, uint32_t nslices, uint32_t tile_keys);
+uint32_t bsx_smem_for(const bsx_config &cfg, uint32_t nslices, uint32_t tile_keys, uint32_t stage_cap);
+uint32_t bsx_stage_cap(const bsx_config &cfg, uint64_t n, uint64_t M);
 void bsx_describe(const bsx_config &cfg, const uint32_t *keys, uint32_t *out, uint64_t n, uint64_t M,
                   bsx::ArrayDesc &a);
 bool bsx_ranges_overlap(const void *a, const void *b, uint64_t bytes);
