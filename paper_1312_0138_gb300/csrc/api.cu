@@ -221,6 +221,7 @@ bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
     uint64_t S = cfg.S ? cfg.S : (1u << 18);
     S = std::max<uint64_t>(S, ceil_div(M, kMaxSlices));
     S = std::min<uint64_t>(S, kMaxSliceValues);
+    S = std::min<uint64_t>(S, (M + 127) / 128 * 128);   // a slice never needs more than M values
     S = std::max<uint64_t>(S, 128);
     cfg.S = round_up_u32((uint32_t)S, 128);
     if (cfg.path == BITSORT_PATH_PARTITION && cfg.layout == LAYOUT_CAPACITY) {
@@ -353,10 +354,24 @@ uint32_t bsx_single_segments(const ArrayDesc &a, Segment *seg, uint32_t *nseg) {
     return t;
 }
 
+// Shrink a configuration until its shared memory fits one CTA: rank
+// emission falls back to word emission, staging to direct stores.
+static bsx_config fit_smem(const bitsort_ctx *c, bsx_config cfg, uint64_t n, uint64_t M) {
+    for (int tries = 0; tries < 3; ++tries) {
+        ArrayDesc probe;
+        bsx_describe(cfg, nullptr, nullptr, n, M, probe);
+        if (bsx_smem_for(cfg, probe.nslices, probe.tile_keys, probe.stage_cap) <= c->smem_optin) break;
+        if (cfg.emit == EMIT_RANK) cfg.emit = EMIT_WORD;
+        else if (cfg.stage) cfg.stage = false;
+        else break;
+    }
+    return cfg;
+}
+
 static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, const uint32_t *keys, uint64_t n,
                                       uint64_t M, uint32_t *out, bitsort_result_t *d_result, cudaStream_t stream,
                                       uint32_t stall) {
-    bsx_config cfg = bsx_sanitize(cfg0, n, M);
+    bsx_config cfg = fit_smem(c, bsx_sanitize(cfg0, n, M), n, M);
     EngineParams p;
     memset(&p, 0, sizeof(p));
     ArrayDesc &a = p.one;

@@ -84,7 +84,7 @@ def test_rank_emission_falls_back_on_skewed_slices(ctx, layout):
     # planned from the average density, so that slice walks its words
     keys = gen.floyd(31, 4000, 4096)
     check(ctx, keys, (1 << 20) - 1, path=bs.PATH_PARTITION, S=4096, layout=layout, emit=1)
-    keys = np.concatenate([gen.floyd(32, 3000, 4096), (gen.floyd(33, 3000, 1 << 20 - 13) + 4096).astype(np.uint32)])
+    keys = np.concatenate([gen.floyd(32, 3000, 4096), (gen.floyd(33, 3000, (1 << 20) - 13) + 4096).astype(np.uint32)])
     keys = np.unique(keys)
     check(ctx, gen.shuffle(34, keys), (1 << 20) + 4096, path=bs.PATH_PARTITION, S=4096, layout=layout, emit=1)
 
