@@ -113,6 +113,32 @@ bitsort_status_t bitsort_ex(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n
  * outcome into the context (and its count through `count`, nullable). */
 bitsort_status_t bitsort_sync_status(bitsort_ctx_t *ctx, bitsort_stream_t stream, uint64_t *count);
 
+/* Sort without allocating any device memory (the paper has no counterpart:
+ * this is a deployment variant of bitsort_ex's partition path).  For callers
+ * that cannot call cudaMalloc: code that runs while a CUDA graph is being
+ * captured (a device allocation is not allowed there), applications whose
+ * device memory is all owned by another allocator (e.g. a framework's
+ * caching allocator that has reserved the whole HBM), and real-time or
+ * certified code that forbids allocation after start-up.
+ *   - keys, out: DEVICE pointers to n uint32 keys / outputs, NOT overlapping
+ *     (out also serves as the partition buffer; keys == out is rejected).
+ *   - d_result: DEVICE pointer (required) that receives the outcome, with
+ *     the same meaning as for bitsort_ex().
+ *   - Limits: max_value < 2^31 (M <= 2^31 values: the fixed scratch holds
+ *     2048 buckets of at most 2^20 values); larger, or keys == out, or a
+ *     null d_result -> BITSORT_ERR_INVALID, nothing enqueued.
+ *   - Scratch: one 49,408-byte __device__ array in the library, held by
+ *     every GPU that loads it until the process exits.  It is shared by all
+ *     calls and keeps the last call's contents; each call clears it first.
+ *     Calls that overlap on the GPU (other streams, other threads) race:
+ *     order them.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress) and sets the kernels'
+ *     shared-memory limit; make that first call before any stream capture.
+ * Allocates nothing: no cudaMalloc/cudaFree, no library allocation. */
+bitsort_status_t bitsort_noalloc(const uint32_t *keys, uint64_t n, uint32_t max_value, uint32_t *out,
+                                 bitsort_result_t *d_result, bitsort_stream_t stream);
+
 /* ---------------------------------------------------------------- batching */
 
 /* One array of a batch.  keys/out are device pointers; the same rules as

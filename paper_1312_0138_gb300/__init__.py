@@ -37,7 +37,7 @@ EXPORTS = [
     "bitsort_server_create", "bitsort_server_submit", "bitsort_server_wait", "bitsort_server_stats",
     "bitsort_server_destroy", "bitsort_autotune", "bitsort_set_config", "bitsort_get_config",
     "bitsort_tune_save", "bitsort_tune_load", "bitsort_set_wait_limit_ms", "bitsort_debug_stalled_launch",
-    "bitsort_kernel_launches",
+    "bitsort_kernel_launches", "bitsort_noalloc",
 ]
 
 
@@ -114,6 +114,7 @@ def _declare(lib):
         "bitsort_set_wait_limit_ms": (st, [p, u32]),
         "bitsort_debug_stalled_launch": (st, [p, p, u64, u32, p, p]),
         "bitsort_kernel_launches": (u64, [p]),
+        "bitsort_noalloc": (st, [p, u64, u32, p, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -367,6 +368,16 @@ def bitsort(keys, max_value: int, out=None, stream=None):
     st = load().bitsort(_ptr(keys) if keys.numel() else None, keys.numel(), int(max_value),
                         _ptr(out) if out.numel() else None, _stream_handle(stream))
     _check(st, "bitsort")
+    return out
+
+
+def bitsort_noalloc(keys, max_value: int, out, result, stream=None):
+    """Enqueue the sort through the C entry point `bitsort_noalloc`, which
+    allocates no device memory: `out` must not overlap `keys`, `result` is a
+    device tensor of 2 int64 receiving (status, count)."""
+    st = load().bitsort_noalloc(_ptr(keys) if keys.numel() else None, keys.numel(), int(max_value),
+                                _ptr(out) if out.numel() else None, result.data_ptr(), _stream_handle(stream))
+    _check(st, "bitsort_noalloc")
     return out
 
 
