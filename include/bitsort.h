@@ -296,6 +296,17 @@ bitsort_status_t bitsort_set_wait_limit_ms(bitsort_ctx_t *ctx, uint32_t ms);
 bitsort_status_t bitsort_debug_stalled_launch(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n,
                                               uint32_t max_value, uint32_t *out, bitsort_stream_t stream);
 
+/* Per-phase timing of single sorts on this context (off by default).  When
+ * on, every bitsort_ex() call records a CUDA event on its stream before its
+ * first kernel and after each kernel (this can cost the overlap between
+ * consecutive kernels).  bitsort_phase_times() waits for the last recorded
+ * event and writes the last call's kernel durations in milliseconds to
+ * ms[0..*count) in launch order, with each kernel's item type in kinds[]
+ * (0 histogram, 1 partition, 2 bucket slices, 3 global scatter, 4 global
+ * scan, -1 persistent); both arrays need room for 8 entries. */
+bitsort_status_t bitsort_set_phase_timing(bitsort_ctx_t *ctx, int enable);
+bitsort_status_t bitsort_phase_times(bitsort_ctx_t *ctx, float *ms, int *kinds, int *count);
+
 /* Number of kernels the library enqueued since the context was created. */
 uint64_t bitsort_kernel_launches(const bitsort_ctx_t *ctx);
 

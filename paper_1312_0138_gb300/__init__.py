@@ -37,7 +37,7 @@ EXPORTS = [
     "bitsort_server_create", "bitsort_server_submit", "bitsort_server_wait", "bitsort_server_stats",
     "bitsort_server_destroy", "bitsort_autotune", "bitsort_set_config", "bitsort_get_config",
     "bitsort_tune_save", "bitsort_tune_load", "bitsort_set_wait_limit_ms", "bitsort_debug_stalled_launch",
-    "bitsort_kernel_launches", "bitsort_noalloc",
+    "bitsort_kernel_launches", "bitsort_noalloc", "bitsort_set_phase_timing", "bitsort_phase_times",
 ]
 
 
@@ -115,6 +115,9 @@ def _declare(lib):
         "bitsort_debug_stalled_launch": (st, [p, p, u64, u32, p, p]),
         "bitsort_kernel_launches": (u64, [p]),
         "bitsort_noalloc": (st, [p, u64, u32, p, p, p]),
+        "bitsort_set_phase_timing": (st, [p, i32]),
+        "bitsort_phase_times": (st, [p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -244,6 +247,18 @@ class Context:
     def debug_stalled_launch(self, keys, max_value: int, out, stream=None):
         _check(load().bitsort_debug_stalled_launch(self.handle, _ptr(keys), keys.numel(), int(max_value),
                                                    _ptr(out), _stream_handle(stream)), "debug_stalled_launch")
+
+    def set_phase_timing(self, enable: bool):
+        _check(load().bitsort_set_phase_timing(self.handle, 1 if enable else 0), "bitsort_set_phase_timing")
+
+    def phase_times(self):
+        """[(kind, ms), ...] of the last single sort's kernels (phase timing on)."""
+        ms = (ctypes.c_float * 8)()
+        kinds = (ctypes.c_int * 8)()
+        cnt = ctypes.c_int(0)
+        _check(load().bitsort_phase_times(self.handle, ms, kinds, ctypes.byref(cnt)), "bitsort_phase_times")
+        names = {-1: "persistent", 0: "hist", 1: "part", 2: "bucket", 3: "gscatter", 4: "gscan"}
+        return [(names.get(kinds[i], kinds[i]), ms[i]) for i in range(cnt.value)]
 
     def kernel_launches(self) -> int:
         return int(load().bitsort_kernel_launches(self.handle))

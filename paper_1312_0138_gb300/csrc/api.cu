@@ -127,6 +127,8 @@ extern "C" bitsort_status_t bitsort_ctx_destroy(bitsort_ctx_t *c) {
     if (c->part) cudaFree(c->part);
     if (c->bitmap) cudaFree(c->bitmap);
     if (c->flush) cudaFree(c->flush);
+    for (int i = 0; i < 9; ++i)
+        if (c->tev[i]) cudaEventDestroy(c->tev[i]);
     delete c;
     return BITSORT_OK;
 }
@@ -180,16 +182,12 @@ bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M) {
     }
     cfg.path = BITSORT_PATH_PARTITION;
     cfg.layout = LAYOUT_CAPACITY;
-    uint64_t target = 4ull * (uint64_t)c->sms;   // four CTAs of 256 threads fit one SM
-    if (n * 8 <= M) {
-        // sparse: rank emission, two CTAs of 512 threads per SM; the slice
-        // takes S/4 bytes (bitmap + prefix) and its staged outputs 5/4 of the
-        // expected 4 n S / M bytes
-        cfg.emit = EMIT_RANK;
-        cfg.threads = 512;
-        const double per_value = 0.25 + 5.0 * (double)n / (double)M;
-        target = std::max<uint64_t>(1, (uint64_t)((double)M * per_value / (double)(c->smem_optin / 2 - 2048)) + 1);
-    }
+    // two slices per SM, word emission, one lane per word, 512 threads: the
+    // best measured rule on GB300 for sparse and medium densities
+    cfg.threads = 512;
+    cfg.wpl = 1;
+    cfg.emit = EMIT_WORD;
+    uint64_t target = 2ull * (uint64_t)c->sms;
     uint64_t S = ceil_div(M, target);
     uint64_t lo = std::max<uint64_t>(4096, ceil_div(M, kMaxSlices));
     S = std::max(S, lo);
@@ -413,10 +411,18 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         uint32_t smem = bsx_smem_for(cfg, a.nslices, a.tile_keys, a.stage_cap);
         if (smem > c->smem_optin) return BITSORT_ERR_INVALID;
         int grid = bsx_grid_for(c, T, smem, p.total_items);
+        if (c->timing) {
+            cudaEventRecord(c->tev[0], stream);
+            c->tkind[0] = -1;
+        }
         int e = engine_launch(p, T, smem, grid, stream);
         if (e != 0) {
             bsx_note_error(e, "engine launch");
             return BITSORT_ERR_CUDA;
+        }
+        if (c->timing) {
+            cudaEventRecord(c->tev[1], stream);
+            c->tcount = 1;
         }
         c->launches.fetch_add(1);
         return BITSORT_OK;
@@ -432,6 +438,10 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         }
         EngineParams q = p;
         q.total_items = items;
+        if (c->timing && launched < 8) {
+            if (launched == 0) cudaEventRecord(c->tev[0], stream);
+            c->tkind[launched] = kind;
+        }
         int per_sm = 1;
         if (kernel_max_blocks_per_sm(kind, T, smem, &per_sm) != 0 || per_sm < 1) per_sm = 1;
         // slice phases and the streaming HIST / GSCATTER phases: one wave of
@@ -445,6 +455,10 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
             return false;
         }
         ++launched;
+        if (c->timing && launched <= 8) {
+            cudaEventRecord(c->tev[launched], stream);
+            c->tcount = launched;
+        }
         return true;
     };
     const uint32_t sl = cfg.emit == EMIT_RANK ? rank_smem_bytes(cfg.S, a.stage_cap)
@@ -542,6 +556,34 @@ extern "C" bitsort_status_t bitsort_debug_stalled_launch(bitsort_ctx_t *c, const
     cfg.threads = 256;
     cfg.S = (uint32_t)std::max<uint64_t>(128, ceil_div(M, 4));  // four buckets
     return launch_single(c, cfg, keys, n, M, out, nullptr, reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+extern "C" bitsort_status_t bitsort_set_phase_timing(bitsort_ctx_t *c, int enable) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    if (enable && !c->tev[0]) {
+        for (int i = 0; i < 9; ++i)
+            if (cudaEventCreate(&c->tev[i]) != cudaSuccess) return BITSORT_ERR_CUDA;
+    }
+    c->timing = enable != 0;
+    c->tcount = 0;
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_phase_times(bitsort_ctx_t *c, float *ms, int *kinds, int *count) {
+    if (!c) c = bsx_default_ctx();
+    if (!c || !ms || !kinds || !count) return BITSORT_ERR_INVALID;
+    *count = 0;
+    if (!c->timing || c->tcount == 0) return BITSORT_OK;
+    if (cudaEventSynchronize(c->tev[c->tcount]) != cudaSuccess) return BITSORT_ERR_CUDA;
+    for (int i = 0; i < c->tcount; ++i) {
+        float t = 0;
+        cudaEventElapsedTime(&t, c->tev[i], c->tev[i + 1]);
+        ms[i] = t;
+        kinds[i] = c->tkind[i];
+    }
+    *count = c->tcount;
+    return BITSORT_OK;
 }
 
 extern "C" uint64_t bitsort_kernel_launches(const bitsort_ctx_t *c) {

@@ -51,6 +51,12 @@ struct bitsort_ctx {
     void *flush = nullptr;        // L2 flush buffer for tuning
     size_t flush_bytes = 0;
 
+    // optional per-phase timing of single sorts
+    bool timing = false;
+    cudaEvent_t tev[9] = {};
+    int tkind[8] = {};
+    int tcount = 0;
+
     std::mutex mu;
     std::map<std::pair<int, int>, bsx_config> table;  // (ceil log2 n, ceil log2 M) -> config
     std::atomic<uint64_t> launches{0};
