@@ -220,7 +220,7 @@ def run_plain(args, w, ws, rank, local):
     if args.path:
         ctx.set_config(n, M - 1, {"fused": 1, "partition": 2, "global": 3}[args.path], args.slice, args.threads,
                        words_per_lane=args.wpl, stage=args.stage, layout=args.layout, persistent=args.persistent,
-                       emit=args.emit)
+                       emit=args.emit, part_stream=args.part_stream)
     cfg = ctx.get_config(n, M - 1)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -278,7 +278,7 @@ def run_plain(args, w, ws, rank, local):
     # algorithmic bytes of one launch of each kernel: 8 B per key (read + write
     # of a 4-byte key) and, for the kernels that build and read the bitmap,
     # M/8 + M/8 bitmap bytes
-    kernel_bytes = {"hist": 4 * n, "part": 8 * n, "gscatter": 4 * n + M // 8, "gscan": 4 * n + M // 8,
+    kernel_bytes = {"hist": 4 * n, "part": 8 * n, "parts": 8 * n, "gscatter": 4 * n + M // 8, "gscan": 4 * n + M // 8,
                     "bucket": 8 * n + M // 4, "persistent": 8 * n + M // 4}
     dom_bytes = kernel_bytes.get(dom, algo_bytes)
     achieved = dom_bytes / (kind_ms[dom] * 1e-3) / 1e9
@@ -461,6 +461,7 @@ def main():
     ap.add_argument("--layout", type=int, default=1)
     ap.add_argument("--persistent", type=int, default=0)
     ap.add_argument("--emit", type=int, default=0)
+    ap.add_argument("--part-stream", type=int, default=0)
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)

@@ -243,6 +243,9 @@ typedef enum {
  *                   bits), through a shared-memory copy of the slice's output
  *                   (for sparse bitmaps; falls back to 0 for a slice with
  *                   more outputs than expected).
+ *   part_stream     1: the partition phase streams its tiles into shared
+ *                   memory with bulk copies (double-buffered) when the keys
+ *                   are 16-byte aligned; 0: the threads load them.
  *   ms              measured time when tuned (output only). */
 typedef struct {
     int32_t path;
@@ -253,6 +256,8 @@ typedef struct {
     uint32_t layout;
     uint32_t persistent;
     uint32_t emit;
+    uint32_t part_stream;
+    uint32_t reserved;
     double ms;
 } bitsort_config_t;
 

@@ -207,8 +207,9 @@ bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M) {
 // slice a multiple of 128 values, FUSED only where one slice covers M.
 bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
     if (cfg.threads != 256 && cfg.threads != 512) cfg.threads = 512;
-    if (cfg.wpl != 1 && cfg.wpl != 2 && cfg.wpl != 4) cfg.wpl = 2;
-    if (cfg.stage) cfg.wpl = 1;
+    if (cfg.wpl != 1 && cfg.wpl != 2 && cfg.wpl != 4 && cfg.wpl != 8) cfg.wpl = 2;
+    if (cfg.stage && cfg.wpl == 2) cfg.wpl = 1;    // staged emission: 1, 4 or 8 words per lane
+    if (!cfg.stage && cfg.wpl == 8) cfg.wpl = 4;   // direct emission: 1, 2 or 4
     if (cfg.layout != LAYOUT_EXACT && cfg.layout != LAYOUT_CAPACITY) cfg.layout = LAYOUT_EXACT;
     if (cfg.path == BITSORT_PATH_FUSED && M > kMaxSliceValues) cfg.path = BITSORT_PATH_PARTITION;
     if (cfg.path == BITSORT_PATH_FUSED) {
@@ -267,7 +268,7 @@ void bsx_describe(const bsx_config &cfg, const uint32_t *keys, uint32_t *out, ui
     a.nslices = (uint32_t)ceil_div(M, cfg.S);
     a.tile_keys = (uint32_t)(kKeysPerThread * cfg.threads);
     a.key_tiles = (uint32_t)ceil_div(n, a.tile_keys);
-    a.wpl = cfg.stage ? 1 : cfg.wpl;
+    a.wpl = cfg.wpl;
     a.stage = cfg.stage ? 1 : 0;
     a.phased = cfg.persistent ? 0 : 1;
     a.layout = cfg.path == BITSORT_PATH_PARTITION ? cfg.layout : LAYOUT_EXACT;
@@ -444,8 +445,8 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         }
         int per_sm = 1;
         if (kernel_max_blocks_per_sm(kind, T, smem, &per_sm) != 0 || per_sm < 1) per_sm = 1;
-        // slice phases and the streaming HIST / GSCATTER phases: one wave of
-        // resident CTAs; PART: a few tiles per CTA
+        // slice phases and the streaming HIST / GSCATTER / PARTS phases: one
+        // wave of resident CTAs; PART: a few tiles per CTA
         const bool one_wave = kind != IT_PART;
         uint64_t grid = (uint64_t)c->sms * (uint64_t)per_sm * (one_wave ? 1u : 8u);
         if (grid > items) grid = items;
@@ -466,13 +467,14 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     bool ok = true;
     if (a.path == BITSORT_PATH_FUSED) {
         ok = phase(IT_BUCKET, 1, sl);
-    } else if (a.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
-        ok = phase(IT_PART, a.key_tiles, part_smem_bytes(a.nslices, a.tile_keys)) &&
-             phase(IT_BUCKET, a.nslices, sl);
     } else if (a.path == BITSORT_PATH_PARTITION) {
-        ok = phase(IT_HIST, a.key_tiles, hist_smem_bytes(a.nslices)) &&
-             phase(IT_PART, a.key_tiles, part_smem_bytes(a.nslices, a.tile_keys)) &&
-             phase(IT_BUCKET, a.nslices, sl);
+        // tiles of 16-byte aligned keys stream through bulk copies
+        const bool stream = ((uintptr_t)keys & 15u) == 0 && cfg.stream_part;
+        const int pk = stream ? (int)IT_PARTS : (int)IT_PART;
+        const uint32_t ps = stream ? part_stream_smem_bytes(a.nslices, a.tile_keys)
+                                   : part_smem_bytes(a.nslices, a.tile_keys);
+        if (a.layout == LAYOUT_EXACT) ok = phase(IT_HIST, a.key_tiles, hist_smem_bytes(a.nslices));
+        ok = ok && phase(pk, a.key_tiles, ps) && phase(IT_BUCKET, a.nslices, sl);
     } else {
         ok = phase(IT_GSCATTER, a.key_tiles, 0) && phase(IT_GSCAN, a.nslices, sl);
     }
@@ -601,6 +603,8 @@ static void to_public(const bsx_config &c, bitsort_config_t *o) {
     o->layout = c.layout;
     o->persistent = c.persistent ? 1 : 0;
     o->emit = c.emit;
+    o->part_stream = c.stream_part ? 1 : 0;
+    o->reserved = 0;
     o->ms = c.ms;
 }
 
@@ -625,6 +629,7 @@ extern "C" bitsort_status_t bitsort_set_config(bitsort_ctx_t *c, uint64_t n, uin
     cfg.layout = in->layout;
     cfg.persistent = in->persistent != 0;
     cfg.emit = in->emit;
+    cfg.stream_part = in->part_stream != 0;
     c->table[key] = bsx_sanitize(cfg, n, M);
     return BITSORT_OK;
 }
@@ -683,6 +688,14 @@ std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_
             for (int lg : {14, 16, 18, 20}) push(BITSORT_PATH_GLOBAL, 1ull << lg, threads, wpl, false, 0);
         }
         if (M <= kMaxSliceValues) push(BITSORT_PATH_FUSED, M, threads, 1, true, LAYOUT_EXACT);
+        for (int k : {1, 2, 3}) {   // partition tiles streamed through bulk copies
+            bsx_config sc = bsx_sanitize(bsx_default_config(c, n, M), n, M);
+            sc.threads = threads;
+            sc.S = (uint32_t)ceil_div(M, (uint64_t)k * c->sms);
+            sc.stream_part = true;
+            sc = bsx_sanitize(sc, n, M);
+            if (sc.path == BITSORT_PATH_PARTITION) out.push_back(sc);
+        }
         for (int k : {2, 4}) {
             bsx_config pc = bsx_sanitize(bsx_default_config(c, n, M), n, M);
             pc.threads = threads;
@@ -786,9 +799,9 @@ extern "C" bitsort_status_t bitsort_tune_save(bitsort_ctx_t *c, const char *path
         const bsx_config &g = kv.second;
         fprintf(f,
                 "%s\n  {\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
-                "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"ms\": %.6f}",
+                "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"part_stream\": %d, \"ms\": %.6f}",
                 first ? "" : ",", kv.first.first, kv.first.second, (int)g.path, g.S, g.threads, g.wpl,
-                g.stage ? 1 : 0, g.layout, g.persistent ? 1 : 0, g.emit, g.ms);
+                g.stage ? 1 : 0, g.layout, g.persistent ? 1 : 0, g.emit, g.stream_part ? 1 : 0, g.ms);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -809,13 +822,13 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
     std::map<std::pair<int, int>, bsx_config> table;
     size_t pos = 0;
     while ((pos = text.find("{\"log2n\"", pos)) != std::string::npos) {
-        int ln = 0, lm = 0, p = 0, th = 0, stage = 0, pers = 0;
+        int ln = 0, lm = 0, p = 0, th = 0, stage = 0, pers = 0, pstream = 0;
         unsigned S = 0, wpl = 0, layout = 0, emit = 0;
         double ms = 0;
         if (sscanf(text.c_str() + pos,
                    "{\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
-                   "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"ms\": %lf",
-                   &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &emit, &ms) != 11)
+                   "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"part_stream\": %d, \"ms\": %lf",
+                   &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &emit, &pstream, &ms) != 12)
             return BITSORT_ERR_INVALID;
         if (p < 1 || p > 3 || (th != 256 && th != 512) || ln < 0 || ln > 64 || lm < 0 || lm > 33)
             return BITSORT_ERR_INVALID;
@@ -828,6 +841,7 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
         cfg.layout = layout;
         cfg.persistent = pers != 0;
         cfg.emit = emit;
+        cfg.stream_part = pstream != 0;
         cfg.ms = ms;
         table[std::make_pair(ln, lm)] = cfg;
         ++pos;

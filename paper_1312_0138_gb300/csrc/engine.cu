@@ -279,70 +279,221 @@ __device__ uint64_t lookback(const EngineParams &P, const ArrayDesc &a, uint32_t
 // a step go through a per-warp shared-memory buffer and leave in coalesced
 // stores; otherwise every lane stores its own positions (consecutive lanes
 // write neighbouring addresses, which stays coalesced at low density).
-template <int WPL, bool STAGE>
+// Writes the set-bit positions of bm[w0, w1) in ascending order to
+// out[base ...]: value = v0 + 32*word + bit (Section II numbering, bit 0
+// first).  A warp step covers U groups of 32 consecutive words; lane l holds
+// word l of every group, so neighbouring lanes write neighbouring outputs
+// (coalesced stores), and the U warp-wide prefix sums that place the lanes'
+// outputs are independent, which hides their shuffle latency.  Each lane
+// writes the four lowest set bits of a word with predicated stores; only
+// words with more set bits walk the rest.
+template <int U>
 __device__ __forceinline__ void emit_words(const uint32_t *bm, uint32_t w0, uint32_t w1, uint32_t v0, uint64_t base,
-                                           uint32_t *out, uint64_t lim, uint32_t *stage) {
+                                           uint32_t *out, uint64_t lim) {
     const int lane = threadIdx.x & 31;
-    for (uint32_t i0 = w0; i0 < w1; i0 += 32 * WPL) {
-        const uint32_t i = i0 + lane * WPL;
-        uint32_t v[WPL];
-        if (i < w1) {
-            if constexpr (WPL == 4) {
-                const uint4 q = *reinterpret_cast<const uint4 *>(bm + i);
-                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-            } else if constexpr (WPL == 2) {
-                const uint2 q = *reinterpret_cast<const uint2 *>(bm + i);
-                v[0] = q.x; v[1] = q.y;
-            } else {
-                v[0] = bm[i];
-            }
-        } else {
+    for (uint32_t i0 = w0; i0 < w1; i0 += 32 * U) {
+        uint32_t v[U], c[U], incl[U];
 #pragma unroll
-            for (int k = 0; k < WPL; ++k) v[k] = 0;
+        for (int u = 0; u < U; ++u) {
+            const uint32_t i = i0 + u * 32 + lane;
+            v[u] = i < w1 ? bm[i] : 0u;
+            c[u] = __popc(v[u]);
+            incl[u] = c[u];
         }
-        uint32_t c = 0;
 #pragma unroll
-        for (int k = 0; k < WPL; ++k) c += __popc(v[k]);
-        const uint32_t incl = warp_incl_scan_u32(c, lane);
-        const uint32_t chunk = __shfl_sync(kFull, incl, 31);
-        uint32_t pos = incl - c;
-        if constexpr (STAGE) {
-            uint32_t val = v0 + i * 32u;
-            uint32_t x = v[0];
-            while (x) {
-                stage[pos++] = val + (__ffs(x) - 1);
-                x &= x - 1;
+        for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t y = __shfl_up_sync(kFull, incl[u], d);
+                if (lane >= d) incl[u] += y;
             }
-            __syncwarp();
-            for (uint32_t k = lane; k < chunk; k += 32)
-                if (base + k < lim) __stcs(out + base + k, stage[k]);   // never past n, whatever the scratch held
-            __syncwarp();
-        } else if (base + chunk <= lim) {   // warp-uniform: the whole step lies inside out[0, n)
-            uint32_t *d = out + base + pos;
+        }
 #pragma unroll
-            for (int k = 0; k < WPL; ++k) {
-                const uint32_t val = v0 + (i + k) * 32u - 1u;
-                uint32_t x = v[k];
-                while (x) {
-                    __stcs(d++, val + __ffs(x));
+        for (int u = 0; u < U; ++u) {
+            const uint32_t chunk = __shfl_sync(kFull, incl[u], 31);
+            const uint32_t pos = incl[u] - c[u];
+            const uint32_t val = v0 + (i0 + u * 32 + lane) * 32u - 1u;
+            uint32_t x = v[u];
+            if (base + chunk <= lim) {   // warp-uniform: the step lies inside out[0, n)
+                uint32_t *d = out + base + pos;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (c[u] > (uint32_t)j) __stcs(d + j, val + __ffs(x));
                     x &= x - 1;
                 }
-            }
-        } else {
-            uint64_t o = base + pos;
-#pragma unroll
-            for (int k = 0; k < WPL; ++k) {
-                const uint32_t val = v0 + (i + k) * 32u;
-                uint32_t x = v[k];
+                if (__any_sync(kFull, x != 0)) {
+                    d += 4;
+                    while (x) {
+                        __stcs(d++, val + __ffs(x));
+                        x &= x - 1;
+                    }
+                }
+            } else {
+                uint64_t o = base + pos;
                 while (x) {
-                    if (o < lim) __stcs(out + o, val + (__ffs(x) - 1));   // never past n
+                    if (o < lim) __stcs(out + o, val + __ffs(x));   // never past n, whatever the scratch held
                     ++o;
                     x &= x - 1;
                 }
             }
+            base += chunk;
         }
-        base += chunk;
     }
+}
+
+// Staged emission: the set-bit positions of many consecutive steps gather in
+// a per-warp shared-memory buffer whose index matches the output address
+// modulo 16 bytes; a full buffer leaves as 16-byte vector stores of whole
+// 128-byte lines (a scalar head and tail around them).  Far fewer, fuller L2
+// write requests than storing each step's handful of positions.
+__device__ __forceinline__ void stage_flush(const uint32_t *stage, uint32_t s0, uint32_t fill, uint32_t *out,
+                                            uint64_t g0, uint64_t lim) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    uint32_t head = (4u - s0) & 3u;
+    if (head > fill) head = fill;
+    if ((uint32_t)lane < head && g0 + lane < lim) __stcs(out + g0 + lane, stage[s0 + lane]);
+    const uint32_t nvec = (fill - head) >> 2;
+    const uint32_t sb = s0 + head;
+    const uint64_t gb = g0 + head;
+    if (gb + 4ull * nvec <= lim) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(stage + sb);
+        uint4 *dst = reinterpret_cast<uint4 *>(out + gb);
+        for (uint32_t k = lane; k < nvec; k += 32) __stcs(dst + k, src[k]);
+    } else {
+        for (uint32_t k = lane; k < 4 * nvec; k += 32)
+            if (gb + k < lim) __stcs(out + gb + k, stage[sb + k]);
+    }
+    const uint32_t t0 = head + 4 * nvec;
+    if ((uint32_t)lane < fill - t0 && g0 + t0 + lane < lim) __stcs(out + g0 + t0 + lane, stage[s0 + t0 + lane]);
+    __syncwarp();
+}
+
+__device__ __forceinline__ void emit_words_staged(const uint32_t *bm, uint32_t w0, uint32_t w1, uint32_t v0,
+                                                  uint64_t base, uint32_t *out, uint64_t lim, uint32_t *stage,
+                                                  uint32_t cap) {
+    const int lane = threadIdx.x & 31;
+    const uintptr_t out_addr = reinterpret_cast<uintptr_t>(out);
+    uint64_t g0 = base;
+    uint32_t s0 = (uint32_t)(((out_addr >> 2) + g0) & 3);
+    uint32_t fill = 0;
+    for (uint32_t i0 = w0; i0 < w1; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        const uint32_t v = i < w1 ? bm[i] : 0u;
+        const uint32_t c = __popc(v);
+        const uint32_t incl = warp_incl_scan_u32(c, lane);
+        const uint32_t chunk = __shfl_sync(kFull, incl, 31);
+        const uint32_t pos = incl - c;
+        if (s0 + fill + chunk > cap) {   // warp-uniform: flush before this step
+            stage_flush(stage, s0, fill, out, g0, lim);
+            g0 += fill;
+            fill = 0;
+            s0 = (uint32_t)(((out_addr >> 2) + g0) & 3);
+        }
+        const uint32_t val = v0 + i * 32u - 1u;
+        uint32_t x = v;
+        if (s0 + chunk <= cap) {
+            uint32_t *d = stage + s0 + fill + pos;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (c > (uint32_t)j) d[j] = val + __ffs(x);
+                x &= x - 1;
+            }
+            if (__any_sync(kFull, x != 0)) {
+                d += 4;
+                while (x) {
+                    *d++ = val + __ffs(x);
+                    x &= x - 1;
+                }
+            }
+            fill += chunk;
+        } else {
+            // one step with more positions than the buffer holds (near-full
+            // words): store it directly
+            uint64_t o = g0 + pos;
+            while (x) {
+                if (o < lim) __stcs(out + o, val + __ffs(x));
+                ++o;
+                x &= x - 1;
+            }
+            g0 += chunk;
+            s0 = (uint32_t)(((out_addr >> 2) + g0) & 3);
+        }
+    }
+    stage_flush(stage, s0, fill, out, g0, lim);
+}
+
+// Staged emission with runs: every lane takes WPL consecutive words, so one
+// warp-wide scan places 32*WPL words, and a lane walks the set bits of its run
+// in one loop (reading its next word from shared memory when the current one
+// is exhausted).  Positions gather in the per-warp buffer and leave through
+// stage_flush.  A step with more positions than the buffer holds (dense
+// words) is written directly.
+template <int WPL>
+__device__ __forceinline__ void emit_runs_staged(const uint32_t *bm, uint32_t w0, uint32_t w1, uint32_t v0,
+                                                 uint64_t base, uint32_t *out, uint64_t lim, uint32_t *stage,
+                                                 uint32_t cap) {
+    const int lane = threadIdx.x & 31;
+    const uintptr_t out_addr = reinterpret_cast<uintptr_t>(out);
+    uint64_t g0 = base;
+    uint32_t s0 = (uint32_t)(((out_addr >> 2) + g0) & 3);
+    uint32_t fill = 0;
+    for (uint32_t i0 = w0; i0 < w1; i0 += 32 * WPL) {
+        const uint32_t i = i0 + lane * WPL;
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < WPL; k += 4) {
+            if (i + k < w1) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(bm + i + k);
+                c += __popc(q.x) + __popc(q.y) + __popc(q.z) + __popc(q.w);
+            }
+        }
+        const uint32_t incl = warp_incl_scan_u32(c, lane);
+        const uint32_t chunk = __shfl_sync(kFull, incl, 31);
+        const uint32_t pos = incl - c;
+        if (s0 + fill + chunk > cap) {   // warp-uniform
+            stage_flush(stage, s0, fill, out, g0, lim);
+            g0 += fill;
+            fill = 0;
+            s0 = (uint32_t)(((out_addr >> 2) + g0) & 3);
+        }
+        uint32_t k = 0;
+        uint32_t x = (c && i < w1) ? bm[i] : 0u;
+        uint32_t val = v0 + i * 32u - 1u;
+        uint32_t left = c;
+        if (s0 + chunk <= cap) {
+            uint32_t *d = stage + s0 + fill + pos;
+            while (left) {
+                if (x) {
+                    *d++ = val + __ffs(x);
+                    x &= x - 1;
+                    --left;
+                } else {
+                    ++k;
+                    x = bm[i + k];   // left > 0: a set bit lies ahead inside the run
+                    val += 32u;
+                }
+            }
+            fill += chunk;
+        } else {
+            uint64_t o = g0 + fill + pos;   // fill == 0 here: the buffer was just flushed
+            while (left) {
+                if (x) {
+                    if (o < lim) __stcs(out + o, val + __ffs(x));
+                    ++o;
+                    x &= x - 1;
+                    --left;
+                } else {
+                    ++k;
+                    x = bm[i + k];
+                    val += 32u;
+                }
+            }
+            g0 += chunk;
+            s0 = (uint32_t)(((out_addr >> 2) + g0) & 3);
+        }
+    }
+    stage_flush(stage, s0, fill, out, g0, lim);
 }
 
 template <int WPL>
@@ -378,7 +529,7 @@ __device__ void slice_count(const EngineParams &P, const ArrayDesc &a, uint32_t 
     w0 = min(words, (uint32_t)warp * wpw);
     w1 = min(words, w0 + wpw);
     uint32_t cnt;
-    if (wpl == 4) cnt = count_words<4>(bm, w0, w1);
+    if (wpl >= 4) cnt = count_words<4>(bm, w0, w1);
     else if (wpl == 2) cnt = count_words<2>(bm, w0, w1);
     else cnt = count_words<1>(bm, w0, w1);
     if (lane == 0) m.wcount[warp] = cnt;
@@ -446,14 +597,17 @@ template <int T>
 __device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t s, const uint32_t *bm,
                              uint32_t words, uint32_t v0, uint32_t *stage_all, SharedMisc &m) {
     const int warp = threadIdx.x >> 5;
-    const uint32_t wpl = a.stage ? 1u : a.wpl;
+    const uint32_t wpl = a.wpl;
     uint32_t w0, w1;
     slice_count<T>(P, a, s, bm, words, wpl, w0, w1, m);
     const uint64_t base = m.excl + m.wbase[warp];
-    if (a.stage) emit_words<1, true>(bm, w0, w1, v0, base, a.out, a.n, stage_all + warp * kStageWords);
-    else if (wpl == 4) emit_words<4, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
-    else if (wpl == 2) emit_words<2, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
-    else emit_words<1, false>(bm, w0, w1, v0, base, a.out, a.n, nullptr);
+    uint32_t *stage = stage_all + warp * kStageWords;
+    if (a.stage && wpl == 8) emit_runs_staged<8>(bm, w0, w1, v0, base, a.out, a.n, stage, kStageWords);
+    else if (a.stage && wpl == 4) emit_runs_staged<4>(bm, w0, w1, v0, base, a.out, a.n, stage, kStageWords);
+    else if (a.stage) emit_words_staged(bm, w0, w1, v0, base, a.out, a.n, stage, kStageWords);
+    else if (wpl == 4) emit_words<4>(bm, w0, w1, v0, base, a.out, a.n);
+    else if (wpl == 2) emit_words<2>(bm, w0, w1, v0, base, a.out, a.n);
+    else emit_words<1>(bm, w0, w1, v0, base, a.out, a.n);
     slice_complete<T>(a, m);
 }
 
@@ -513,6 +667,93 @@ __device__ void item_hist(const EngineParams &P, const ArrayDesc &a, uint32_t ti
 // 32-bit (the buffer has at most 2^32 entries): run start minus the tile-local
 // prefix is kept per bin (delta), so a key's position is delta[b] + its index
 // in the reordered tile; lim[b] ends the part of the run that fits.
+//
+// part_tile() does everything after the keys are in registers: x[j] holds
+// tile element j*T + threadIdx.x (valid while that index < nkeys).  `sorted`
+// may be the buffer the keys came from: it is written only after a barrier
+// that follows every thread's reads.
+template <int T>
+__device__ void part_tile(const ArrayDesc &a, const uint32_t (&x)[kKeysPerThread], uint32_t nkeys, uint32_t *hist,
+                          uint32_t *delta, uint32_t *lim, uint32_t *sorted, uint16_t *sorted_b, SharedMisc &m) {
+    constexpr int K = kKeysPerThread;
+    const uint32_t nb = a.nslices;
+    const uint32_t nbins = nb + 1;
+    const bool capacity = a.layout == LAYOUT_CAPACITY;
+    const uint64_t magic = a.div_magic;
+    const uint32_t maxv = (uint32_t)(a.M - 1);
+    uint32_t br[K];   // bin << 16 | rank in the tile
+    bool bad = false;
+    if (nkeys == (uint32_t)a.tile_keys) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const bool in = x[j] <= maxv;
+            bad |= !in;
+            const uint32_t bin = in ? bucket_of(x[j], magic) : nb;
+            br[j] = (bin << 16) | atomicAdd(&hist[bin], 1u);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            br[j] = 0xFFFFFFFFu;
+            if ((uint32_t)j * T + threadIdx.x < nkeys) {
+                const bool in = x[j] <= maxv;
+                bad |= !in;
+                const uint32_t bin = in ? bucket_of(x[j], magic) : nb;
+                br[j] = (bin << 16) | atomicAdd(&hist[bin], 1u);
+            }
+        }
+    }
+    if (capacity) {
+        bad = __syncthreads_or(bad);
+        if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
+    } else {
+        __syncthreads();   // (the histogram pass reports keys above max_value)
+    }
+    // reserve each bucket's run (needs the counts), then turn counts into prefixes
+    for (uint32_t i = threadIdx.x; i < nbins; i += T) {
+        const uint32_t c = hist[i];
+        uint32_t start = 0, fit = 0;
+        if (c && i < nb) {
+            const uint32_t at = atomicAdd(&a.cursor[i], c);
+            if (capacity) {
+                const uint64_t cap = a.cap;
+                start = (uint32_t)((uint64_t)i * cap + at);
+                fit = at >= cap ? 0u : (uint32_t)min((uint64_t)c, cap - at);
+                if (fit < c) atomicOr(&a.sync[SY_OVERFLOW], 1u);   // only with repeated keys
+            } else {
+                const uint64_t st = __ldcg(&a.offsets[i]) + at;
+                start = (uint32_t)st;
+                fit = st >= a.n ? 0u : (uint32_t)min((uint64_t)c, a.n - st);   // a sane scratch never clips
+            }
+        }
+        delta[i] = start;
+        lim[i] = fit;
+    }
+    block_exclusive_scan_u32<T>(nbins, hist, hist, m);
+    for (uint32_t i = threadIdx.x; i < nbins; i += T) {
+        const uint32_t p = hist[i];
+        delta[i] -= p;   // position = delta + index in the reordered tile (mod 2^32)
+        lim[i] += p;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if (br[j] != 0xFFFFFFFFu) {
+            const uint32_t bin = br[j] >> 16;
+            const uint32_t at = hist[bin] + (br[j] & 0xFFFFu);
+            sorted[at] = x[j];
+            sorted_b[at] = (uint16_t)bin;
+        }
+    }
+    __syncthreads();
+    uint32_t *part = a.part;
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < nkeys; i += T) {
+        const uint32_t bin = sorted_b[i];
+        if (i < lim[bin]) part[delta[bin] + i] = sorted[i];
+    }
+}
+
 template <int T>
 __device__ void item_part(const EngineParams &P, const ArrayDesc &a, uint32_t tile, char *smem, SharedMisc &m) {
     constexpr int K = kKeysPerThread;
@@ -538,96 +779,172 @@ __device__ void item_part(const EngineParams &P, const ArrayDesc &a, uint32_t ti
         const uint64_t lo = (uint64_t)tile * a.tile_keys;
         const uint64_t hi = min(lo + a.tile_keys, a.n);
         const uint32_t nkeys = (uint32_t)(hi - lo);
-        const uint64_t magic = a.div_magic;
-        const uint32_t maxv = (uint32_t)(a.M - 1);
-        uint32_t x[K], br[K];   // key; bin << 16 | rank in the tile
-        bool bad = false;
+        uint32_t x[K];
         if (nkeys == (uint32_t)a.tile_keys && (reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0) {
-            // full tile: K keys per thread, 128-bit loads, no per-key checks
+            // full tile: K keys per thread, 128-bit loads
             const uint4 *src = reinterpret_cast<const uint4 *>(a.keys + lo);
 #pragma unroll
             for (int j = 0; j < K / 4; ++j) {
                 const uint4 q = __ldcs(src + j * T + threadIdx.x);
                 x[4 * j] = q.x; x[4 * j + 1] = q.y; x[4 * j + 2] = q.z; x[4 * j + 3] = q.w;
             }
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const bool in = x[j] <= maxv;
-                bad |= !in;
-                const uint32_t bin = in ? bucket_of(x[j], magic) : nb;
-                br[j] = (bin << 16) | atomicAdd(&hist[bin], 1u);
-            }
+            // element order j*T + tid inside the tile is a permutation of the
+            // (4*(j'*T + tid) + r) load order; ranks only need some order
         } else {
-            // tail tile or unaligned keys: element-wise, index j*T + tid
 #pragma unroll
             for (int j = 0; j < K; ++j) {
                 const uint32_t e = (uint32_t)j * T + threadIdx.x;
-                br[j] = 0xFFFFFFFFu;
-                x[j] = 0;
-                if (e < nkeys) {
-                    x[j] = __ldcs(a.keys + lo + e);
-                    const bool in = x[j] <= maxv;
-                    bad |= !in;
-                    const uint32_t bin = in ? bucket_of(x[j], magic) : nb;
-                    br[j] = (bin << 16) | atomicAdd(&hist[bin], 1u);
-                }
+                x[j] = e < nkeys ? __ldcs(a.keys + lo + e) : 0u;
             }
         }
-        if (capacity) {
-            bad = __syncthreads_or(bad);
-            if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
-        } else {
-            __syncthreads();   // (the histogram pass reports keys above max_value)
-        }
-        // reserve each bucket's run (needs the counts), then turn counts into prefixes
-        for (uint32_t i = threadIdx.x; i < nbins; i += T) {
-            const uint32_t c = hist[i];
-            uint32_t start = 0, fit = 0;
-            if (c && i < nb) {
-                const uint32_t at = atomicAdd(&a.cursor[i], c);
-                if (capacity) {
-                    const uint64_t cap = a.cap;
-                    start = (uint32_t)((uint64_t)i * cap + at);
-                    fit = at >= cap ? 0u : (uint32_t)min((uint64_t)c, cap - at);
-                    if (fit < c) atomicOr(&a.sync[SY_OVERFLOW], 1u);   // only with repeated keys
-                } else {
-                    const uint64_t st = __ldcg(&a.offsets[i]) + at;
-                    start = (uint32_t)st;
-                    fit = st >= a.n ? 0u : (uint32_t)min((uint64_t)c, a.n - st);   // a sane scratch never clips
-                }
-            }
-            delta[i] = start;
-            lim[i] = fit;
-        }
-        block_exclusive_scan_u32<T>(nbins, hist, hist, m);
-        for (uint32_t i = threadIdx.x; i < nbins; i += T) {
-            const uint32_t p = hist[i];
-            delta[i] -= p;   // position = delta + index in the reordered tile (mod 2^32)
-            lim[i] += p;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (br[j] != 0xFFFFFFFFu) {
-                const uint32_t bin = br[j] >> 16;
-                const uint32_t at = hist[bin] + (br[j] & 0xFFFFu);
-                sorted[at] = x[j];
-                sorted_b[at] = (uint16_t)bin;
-            }
-        }
-        __syncthreads();
-        uint32_t *part = a.part;
-#pragma unroll 4
-        for (uint32_t i = threadIdx.x; i < nkeys; i += T) {
-            const uint32_t bin = sorted_b[i];
-            if (i < lim[bin]) part[delta[bin] + i] = sorted[i];
-        }
+        part_tile<T>(a, x, nkeys, hist, delta, lim, sorted, sorted_b, m);
     }
     if (!a.phased) {
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(&a.sync[SY_PART_DONE], 1u);
     }
+}
+
+// ---------------------------------------------- bulk copies (TMA) + mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+// bytes from global src to shared dst (both 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the given phase of an mbarrier (a bulk copy of this CTA's
+// own); false after `limit_ns` (then the caller reports a timeout).
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if ((it & 63) == 63 && now_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+// Streaming PART (one kernel, one CTA per resident slot): a CTA takes tiles
+// t, t + G, t + 2G, ...  While tile k is ranked, reserved, reordered and
+// written, the bulk-copy engine already brings tile k+1 into the other
+// buffer; a tile's landing buffer then serves as its reordered copy.  Tiles
+// that are not whole, or keys that are not 16-byte aligned, are loaded by
+// the threads instead.
+template <int T>
+__device__ void part_stream(const EngineParams &P, const ArrayDesc &a, char *smem, SharedMisc &m) {
+    constexpr int K = kKeysPerThread;
+    const uint32_t nb = a.nslices;
+    const uint32_t nbins = nb + 1;
+    // layout (as part_stream_smem_bytes): bins | bucket tags | two landing buffers | two mbarriers
+    const uint32_t off_tags = ((nbins * 12u) + 127u) & ~127u;
+    const uint32_t off_buf = off_tags + ((a.tile_keys * 2u + 127u) & ~127u);
+    const uint32_t off_mbar = off_buf + 2u * a.tile_keys * 4u;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *delta = hist + nbins;
+    uint32_t *lim = delta + nbins;
+    uint16_t *tags = reinterpret_cast<uint16_t *>(smem + off_tags);
+    uint32_t *buf0 = reinterpret_cast<uint32_t *>(smem + off_buf);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + off_mbar);
+    const uint32_t ntiles = a.key_tiles;
+    const uint32_t G = gridDim.x;
+    const uint32_t tile_bytes = a.tile_keys * 4u;
+    const bool aligned = (reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0;
+    auto whole = [&](uint32_t t) { return aligned && (uint64_t)(t + 1) * a.tile_keys <= a.n; };
+
+    uint32_t t = blockIdx.x;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && t < ntiles && whole(t)) {
+        mbar_expect_tx(&mbar[0], tile_bytes);
+        bulk_load(buf0, a.keys + (uint64_t)t * a.tile_keys, tile_bytes, &mbar[0]);
+    }
+    // per buffer: completed uses (mbarrier phase parity) and a copy not yet waited for
+    uint32_t uses0 = 0, uses1 = 0;
+    bool pend0 = t < ntiles && whole(t), pend1 = false;
+    bool ok = true;
+    for (uint32_t k = 0; t < ntiles; ++k, t += G) {
+        const uint32_t b = k & 1u;
+        uint32_t *cur = buf0 + (b ? a.tile_keys : 0u);
+        uint32_t *nxt = buf0 + (b ? 0u : a.tile_keys);
+        const uint32_t tn = t + G;
+        if (tn < ntiles && whole(tn)) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();   // this buffer was last read and written by the threads
+                mbar_expect_tx(&mbar[b ^ 1u], tile_bytes);
+                bulk_load(nxt, a.keys + (uint64_t)tn * a.tile_keys, tile_bytes, &mbar[b ^ 1u]);
+            }
+            if (b) pend0 = true;
+            else pend1 = true;
+        }
+        for (uint32_t i = threadIdx.x; i < nbins; i += T) hist[i] = 0;
+        const uint64_t lo = (uint64_t)t * a.tile_keys;
+        const uint32_t nkeys = (uint32_t)(min(lo + a.tile_keys, a.n) - lo);
+        uint32_t x[K];
+        if (whole(t)) {
+            const uint32_t use = b ? uses1 : uses0;
+            if (!mbar_wait(&mbar[b], use & 1u, P.wait_limit_ns)) ok = false;
+            if (b) {
+                ++uses1;
+                pend1 = false;
+            } else {
+                ++uses0;
+                pend0 = false;
+            }
+            const uint4 *src = reinterpret_cast<const uint4 *>(cur);
+#pragma unroll
+            for (int j = 0; j < K / 4; ++j) {
+                const uint4 q = src[j * T + threadIdx.x];
+                x[4 * j] = q.x; x[4 * j + 1] = q.y; x[4 * j + 2] = q.z; x[4 * j + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const uint32_t e = (uint32_t)j * T + threadIdx.x;
+                x[j] = e < nkeys ? __ldcs(a.keys + lo + e) : 0u;
+            }
+        }
+        __syncthreads();   // hist zeroed; every thread holds its keys (the buffer is free)
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicOr(&a.sync[SY_TIMEOUT], 1u);
+            break;
+        }
+        part_tile<T>(a, x, nkeys, hist, delta, lim, cur, tags, m);
+        __syncthreads();
+    }
+    // no bulk copy of this CTA may still be in flight when it exits (only
+    // after a timeout can one be left un-waited)
+    if (pend0) mbar_wait(&mbar[0], uses0 & 1u, P.wait_limit_ns);
+    if (pend1) mbar_wait(&mbar[1], uses1 & 1u, P.wait_limit_ns);
 }
 
 template <int T>
@@ -713,7 +1030,7 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     if (total > a.stage_cap) {
         // more outputs than the staging room (skewed keys): walk the words instead
         slice_lookback<T>(P, a, b, m);
-        emit_words<1, false>(bm, w0, w1, (uint32_t)v0, m.excl + m.wbase[warp], a.out, a.n, nullptr);
+        emit_words<1>(bm, w0, w1, (uint32_t)v0, m.excl + m.wbase[warp], a.out, a.n);
         slice_complete<T>(a, m);
         return;
     }
@@ -891,6 +1208,9 @@ __global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constan
                 __threadfence();
             }
         }
+    } else if constexpr (TYPE == IT_PARTS) {
+        part_stream<T>(P, a, smem, m);
+        pdl_trigger();
     } else if constexpr (TYPE == IT_PART) {
         for (uint32_t t = blockIdx.x; t < P.total_items; t += gridDim.x) {
             item_part<T>(P, a, t, smem, m);
@@ -922,6 +1242,7 @@ static KernelFn kernel_for(int kind, int threads) {
             case IT_BUCKET: return phase_kernel<256, IT_BUCKET>;
             case IT_GSCATTER: return phase_kernel<256, IT_GSCATTER>;
             case IT_GSCAN: return phase_kernel<256, IT_GSCAN>;
+            case IT_PARTS: return phase_kernel<256, IT_PARTS>;
         }
     } else if (threads == 512) {
         switch (kind) {
@@ -931,13 +1252,14 @@ static KernelFn kernel_for(int kind, int threads) {
             case IT_BUCKET: return phase_kernel<512, IT_BUCKET>;
             case IT_GSCATTER: return phase_kernel<512, IT_GSCATTER>;
             case IT_GSCAN: return phase_kernel<512, IT_GSCAN>;
+            case IT_PARTS: return phase_kernel<512, IT_PARTS>;
         }
     }
     return nullptr;
 }
 
 int engine_set_smem_limit(int threads, uint32_t smem_bytes) {
-    for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN}) {
+    for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN, (int)IT_PARTS}) {
         KernelFn f = kernel_for(kind, threads);
         if (!f) return (int)cudaErrorInvalidValue;
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);

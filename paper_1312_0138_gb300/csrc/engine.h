@@ -29,7 +29,8 @@
 
 namespace bsx {
 
-enum ItemType : uint32_t { IT_HIST = 0, IT_PART = 1, IT_BUCKET = 2, IT_GSCATTER = 3, IT_GSCAN = 4 };
+enum ItemType : uint32_t { IT_HIST = 0, IT_PART = 1, IT_BUCKET = 2, IT_GSCATTER = 3, IT_GSCAN = 4,
+                           IT_PARTS = 5 /* PART tiles streamed through bulk copies (phase kernel only) */ };
 
 enum SyncSlot : uint32_t {
     SY_HIST_DONE = 0,     // HIST tiles finished
@@ -119,7 +120,7 @@ struct EngineParams {
 };
 
 // Shared-memory sizes (bytes) an item type needs for a given configuration.
-constexpr uint32_t kStageWords = 1024;  // per warp: 32 words x 32 bits
+constexpr uint32_t kStageWords = 1024 + 4;  // per warp: staged positions (+ room for the 16-byte alignment shift)
 inline uint32_t slice_smem_bytes(uint32_t S, int threads, bool stage) {
     uint32_t words = (S + 31) / 32;
     uint32_t w4 = (words + 3) & ~3u;
@@ -136,6 +137,12 @@ inline uint32_t part_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
     return (nslices + 1) * 12u + tile_keys * 6u + 16u;
 }
 inline uint32_t hist_smem_bytes(uint32_t nslices) { return nslices * 4u; }
+// streaming PART: bins, bucket tags, two landing buffers, two mbarriers (128-byte aligned parts)
+inline uint32_t part_stream_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
+    const uint32_t a = ((nslices + 1) * 12u + 127u) & ~127u;
+    const uint32_t t = (tile_keys * 2u + 127u) & ~127u;
+    return a + t + 2u * tile_keys * 4u + 16u;
+}
 
 constexpr int kKeysPerThread = 16;   // keys per thread in one HIST/PART/GSCATTER tile
 constexpr uint32_t kMaxSlices = 8192;   // bucket ids fit 16 bits in the partition tile

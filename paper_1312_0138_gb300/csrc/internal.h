@@ -22,6 +22,7 @@ struct bsx_config {
     uint32_t wpl = 2;        // bitmap words per lane in the scan (1, 2, 4)
     bool stage = false;      // stage set-bit positions per warp in shared memory
     uint32_t emit = 0;       // bsx::EMIT_WORD (0) or bsx::EMIT_RANK (1)
+    bool stream_part = false; // phased PARTITION: stream tiles through bulk copies when keys are 16-byte aligned
     double ms = 0;           // measured time when tuned (0 = not measured)
 };
 

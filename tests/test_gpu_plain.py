@@ -46,6 +46,14 @@ CONFIGS = [
     ("cap_odd_persist", bs.PATH_PARTITION, 883_072, 256, dict(layout=1, persistent=1, words_per_lane=2)),
     ("exact_odd_persist_stage", bs.PATH_PARTITION, 883_072, 512, dict(layout=0, persistent=1, stage=1)),
     ("exact_S4096_persist_w4", bs.PATH_PARTITION, 4096, 256, dict(layout=0, persistent=1, words_per_lane=4)),
+    ("cap_S1M_runs8", bs.PATH_PARTITION, 1 << 20, 512, dict(layout=1, stage=1, words_per_lane=8)),
+    ("cap_stream_S64K", bs.PATH_PARTITION, 1 << 16, 512, dict(layout=1, part_stream=1)),
+    ("exact_stream_odd_256", bs.PATH_PARTITION, 300_032, 256, dict(layout=0, part_stream=1)),
+    ("exact_odd_runs4_256", bs.PATH_PARTITION, 300_032, 256, dict(layout=0, stage=1, words_per_lane=4)),
+    ("cap_S4096_runs8_persist", bs.PATH_PARTITION, 4096, 512, dict(layout=1, stage=1, words_per_lane=8,
+                                                                    persistent=1)),
+    ("fused_runs8", bs.PATH_FUSED, 0, 512, dict(stage=1, words_per_lane=8)),
+    ("global_S64K_runs4", bs.PATH_GLOBAL, 1 << 16, 512, dict(stage=1, words_per_lane=4)),
     ("rank_cap_S64K", bs.PATH_PARTITION, 1 << 16, 512, dict(layout=1, emit=1)),
     ("rank_exact_S4096_256", bs.PATH_PARTITION, 4096, 256, dict(layout=0, emit=1)),
     ("rank_exact_odd_persist", bs.PATH_PARTITION, 300_032, 512, dict(layout=0, emit=1, persistent=1)),
@@ -75,6 +83,8 @@ STRATS = [
     ("rank_exact", dict(path=bs.PATH_PARTITION, S=4096, layout=0, emit=1)),
     ("rank_capacity", dict(path=bs.PATH_PARTITION, S=4096, layout=1, emit=1)),
     ("rank_fused", dict(path=bs.PATH_FUSED, emit=1)),
+    ("runs8", dict(path=bs.PATH_PARTITION, S=4096, layout=1, stage=1, words_per_lane=8)),
+    ("stream", dict(path=bs.PATH_PARTITION, S=4096, layout=1, part_stream=1)),
 ]
 
 
