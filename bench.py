@@ -311,6 +311,8 @@ def run_plain(args, w, ws, rank, local):
     assert int(hres[0]) & 0xFFFFFFFF == bs.OK and int(hres[1]) == n
     assert bool(np.all(np.diff(hout.numpy().view(np.uint32)[:1 << 20].astype(np.int64)) > 0))
 
+    cub = time_cub(keys, M, flush, stream, args.steps) if not args.no_cub else None
+
     if rank != 0:
         return
     cpu = time_oracle(keys_np, M - 1, budget_s=args.cpu_budget,
@@ -337,8 +339,42 @@ def run_plain(args, w, ws, rank, local):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "comparison": cub,
     }
     print(json.dumps(line), flush=True)
+
+
+def time_cub(keys, M, flush, stream, steps):
+    """cub::DeviceRadixSort::SortKeys on the same keys and GPU (comparison
+    point only; a multiset sort on bits [0, ceil(log2 M)))."""
+    import ctypes
+    import torch
+    path = os.path.join(ROOT, "paper_1312_0138_gb300", "compare", "libcubcompare.so")
+    if not os.path.exists(path):
+        return {"unavailable": "libcubcompare.so not built"}
+    lib = ctypes.CDLL(path)
+    lib.cub_radix_sort_keys.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.c_void_p]
+    lib.cub_radix_sort_keys.restype = ctypes.c_int
+    end_bit = max(1, (M - 1).bit_length())
+    out = torch.empty_like(keys)
+    n = keys.numel()
+    h = stream.cuda_stream
+    assert lib.cub_radix_sort_keys(keys.data_ptr(), out.data_ptr(), n, end_bit, h) == 0
+    torch.cuda.synchronize()
+    reps = max(3, min(steps, 100))
+    ms = []
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lib.cub_radix_sort_keys(keys.data_ptr(), out.data_ptr(), n, end_bit, h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = float(np.median(ms))
+    return {"impl": "cub::DeviceRadixSort::SortKeys", "end_bit": end_bit, "ms": t,
+            "gkeys_s": n / (t * 1e-3) / 1e9}
 
 
 def run_batched(args, ws, rank, local):
@@ -434,6 +470,17 @@ def run_served(args, ws, rank, local):
     stats = srv.stats()
     srv.close()
     total = sum(n for _, n, _ in spec)
+    # the same requests as one plain call after another (one context, one stream)
+    ctx = bs.Context(local)
+    for _, k, mv, o in reqs[:3]:
+        ctx.sort_async(k, mv, out=o)
+    torch.cuda.synchronize()
+    p0 = time.perf_counter()
+    for _, k, mv, o in reqs:
+        ctx.sort_async(k, mv, out=o)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - p0
+    ctx.close()
     line = {"metric": METRIC, "value": total / wall / 1e9, "unit": "Gkeys/s", "n_gpus": ws, "steps": count,
             "warmup": 0, "ms_per_step": wall * 1e3 / count, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -441,7 +488,9 @@ def run_served(args, ws, rank, local):
                                    f"[2^10,2^26], max_value log-uniform [2^16,2^32-1], 40 GiB budget",
                        "p50_ms": float(np.percentile(lats, 50)) * 1e3,
                        "p99_ms": float(np.percentile(lats, 99)) * 1e3, "batches": stats["batches"],
-                       "max_concurrent_batches": stats["max_concurrent"], "total_keys": total}}
+                       "max_concurrent_batches": stats["max_concurrent"], "total_keys": total,
+                       "plain_calls_s": plain_s, "plain_calls_gkeys_s": total / plain_s / 1e9,
+                       "served_over_plain": (total / wall) / (total / plain_s)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -464,6 +513,7 @@ def main():
     ap.add_argument("--part-stream", type=int, default=0)
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cub", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--batch-count", type=int, default=4096)

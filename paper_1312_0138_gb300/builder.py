@@ -72,5 +72,23 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     return LIB
 
 
+COMPARE_SRC = os.path.join(HERE, "compare", "cub_radix.cu")
+COMPARE_LIB = os.path.join(HERE, "compare", "libcubcompare.so")
+
+
+def build_compare(force: bool = False) -> str:
+    """libcubcompare.so: cub::DeviceRadixSort, the benchmark's comparison point."""
+    if not force and os.path.exists(COMPARE_LIB) and os.path.getmtime(COMPARE_LIB) >= os.path.getmtime(COMPARE_SRC):
+        return COMPARE_LIB
+    tmp = COMPARE_LIB + f".{os.getpid()}.tmp"
+    cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+                             "-o", tmp, COMPARE_SRC]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {COMPARE_SRC}:\n{res.stdout}\n{res.stderr}")
+    os.replace(tmp, COMPARE_LIB)
+    return COMPARE_LIB
+
+
 if __name__ == "__main__":
     build(force=True, verbose=True)

@@ -291,14 +291,29 @@ template <int U>
 __device__ __forceinline__ void emit_words(const uint32_t *bm, uint32_t w0, uint32_t w1, uint32_t v0, uint64_t base,
                                            uint32_t *out, uint64_t lim) {
     const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;   // lanes below this one
     for (uint32_t i0 = w0; i0 < w1; i0 += 32 * U) {
         uint32_t v[U], c[U], incl[U];
+        bool single = true;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t i = i0 + u * 32 + lane;
             v[u] = i < w1 ? bm[i] : 0u;
             c[u] = __popc(v[u]);
             incl[u] = c[u];
+            single &= c[u] <= 1u;
+        }
+        if (__all_sync(kFull, single)) {
+            // sparse step: no word holds more than one set bit, so a lane's
+            // output index is the number of non-empty words below it
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t nz = __ballot_sync(kFull, v[u] != 0);
+                const uint64_t o = base + __popc(nz & lt);
+                if (v[u] && o < lim) __stcs(out + o, v0 + (i0 + u * 32 + lane) * 32u + (__ffs(v[u]) - 1));
+                base += __popc(nz);
+            }
+            continue;
         }
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -524,14 +539,13 @@ __device__ void slice_count(const EngineParams &P, const ArrayDesc &a, uint32_t 
                             bool with_lookback = true) {
     constexpr int NW = T / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t step = 32u * wpl;
+    // warp ranges are whole multiples of 32 * max(wpl, 4) words: every
+    // emitter's steps fit, and the count reads 4 words per lane
+    const uint32_t step = 32u * max(wpl, 4u);
     const uint32_t wpw = (((words + NW - 1) / NW) + step - 1) / step * step;
     w0 = min(words, (uint32_t)warp * wpw);
     w1 = min(words, w0 + wpw);
-    uint32_t cnt;
-    if (wpl >= 4) cnt = count_words<4>(bm, w0, w1);
-    else if (wpl == 2) cnt = count_words<2>(bm, w0, w1);
-    else cnt = count_words<1>(bm, w0, w1);
+    const uint32_t cnt = count_words<4>(bm, w0, w1);
     if (lane == 0) m.wcount[warp] = cnt;
     __syncthreads();
     if (warp == 0) {
