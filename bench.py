@@ -222,7 +222,7 @@ def run_plain(args, w, ws, rank, local):
                        words_per_lane=args.wpl, stage=args.stage, layout=args.layout, persistent=args.persistent,
                        emit=args.emit, part_stream=args.part_stream)
     cfg = ctx.get_config(n, M - 1)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(args.flush)
     stream = torch.cuda.current_stream()
 
     # correctness of the measured configuration (one sort, checked on device)
@@ -323,7 +323,8 @@ def run_plain(args, w, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": w["desc"], "n": n, "max_value": M - 1, "keys": w["method"],
-                   "l2": "flushed between timed steps (512 MiB write, outside the step events)",
+                   "l2": f"flushed between timed steps ({args.flush}: 512 MiB write"
+                         f"{' + 512 MiB read' if args.flush == 'write+read' else ''}, outside the step events)",
                    "plan": cfg, "wall_s": wall},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": dom_bytes,
@@ -342,6 +343,26 @@ def run_plain(args, w, ws, rank, local):
         "comparison": cub,
     }
     print(json.dumps(line), flush=True)
+
+
+class L2Flush:
+    """Evicts the workload from L2 between timed steps, outside the timed
+    events: writes a 512 MiB buffer (larger than the 126 MB L2); mode
+    'write+read' then reads a second 512 MiB buffer, so that the L2 holds
+    clean lines of an unrelated buffer instead of 512 MiB of dirty flush data
+    whose write-back would land inside the next timed step."""
+
+    def __init__(self, mode="write+read"):
+        import torch
+        self.mode = mode
+        self.w = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        self.r = torch.ones(128 << 20, dtype=torch.float32, device="cuda") if mode == "write+read" else None
+        self.sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def fill_(self, v):
+        self.w.fill_(v)
+        if self.r is not None:
+            self.sink += self.r.sum()
 
 
 def time_cub(keys, M, flush, stream, steps):
@@ -396,6 +417,8 @@ def run_batched(args, ws, rank, local):
         outs.append(o)
         arrays.append((k, M - 1, o))
         total += n
+    if args.tune:
+        ctx.batch_autotune(arrays)
     plan = ctx.plan(arrays)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -430,6 +453,7 @@ def run_batched(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"batched bitsort, {len(spec)} arrays in one persistent launch (CUDA graph), "
                                    f"n log-uniform [2^10,2^22], max_value log-uniform [2^12,2^26], density [1/64,1/2]",
+                       "batch_policy": ctx.get_batch_config(),
                        "total_keys": total, "plain_launches_ms": plain_ms,
                        "plain_launches_gkeys_s": total / (plain_ms * 1e-3) / 1e9,
                        "speedup_vs_plain_launches": plain_ms / batched_ms},
@@ -514,6 +538,7 @@ def main():
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cub", action="store_true")
+    ap.add_argument("--flush", default="write+read", choices=["write", "write+read"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--batch-count", type=int, default=4096)

@@ -109,6 +109,23 @@ bitsort_status_t bitsort(const uint32_t *keys, size_t n, uint32_t max_value, uin
 bitsort_status_t bitsort_ex(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n, uint32_t max_value,
                             uint32_t *out, bitsort_result_t *d_result, bitsort_stream_t stream);
 
+/* Sort n distinct SIGNED int32 keys in [min_value, max_value] into ascending
+ * signed order (Section III, Algorithm 1's second function: the paper sorts
+ * negative and nonnegative keys apart and joins them; here every key is
+ * shifted by -min_value modulo 2^32, which maps the range onto
+ * 0 .. max_value - min_value in the same order, and sorted as unsigned keys
+ * with the shift undone on output).
+ *   - keys, out: DEVICE pointers to n int32 values; keys == out sorts in
+ *     place; other overlaps -> BITSORT_ERR_INVALID.
+ *   - min_value > max_value, n > max_value - min_value + 1 (the keys cannot
+ *     be distinct), or misaligned pointers -> BITSORT_ERR_INVALID.
+ *   - A key outside [min_value, max_value] -> BITSORT_ERR_KEY_RANGE, repeated
+ *     keys -> BITSORT_ERR_DUPLICATE, both reported through d_result (or the
+ *     context) like bitsort_ex(); the whole int32 range (min INT32_MIN, max
+ *     INT32_MAX) is allowed. */
+bitsort_status_t bitsort_i32(bitsort_ctx_t *ctx, const int32_t *keys, uint64_t n, int32_t min_value,
+                             int32_t max_value, int32_t *out, bitsort_result_t *d_result, bitsort_stream_t stream);
+
 /* Wait for `stream`, then return the status of the last sort that wrote its
  * outcome into the context (and its count through `count`, nullable). */
 bitsort_status_t bitsort_sync_status(bitsort_ctx_t *ctx, bitsort_stream_t stream, uint64_t *count);
@@ -181,6 +198,7 @@ const bitsort_result_t *bitsort_batch_plan_device_results(const bitsort_batch_pl
 
 bitsort_status_t bitsort_batch_plan_destroy(bitsort_batch_plan_t *plan);
 
+
 /* ----------------------------------------------------------------- serving */
 
 typedef struct bitsort_server bitsort_server_t;
@@ -246,6 +264,10 @@ typedef enum {
  *   part_stream     1: the partition phase streams its tiles into shared
  *                   memory with bulk copies (double-buffered) when the keys
  *                   are 16-byte aligned; 0: the threads load them.
+ *   summary         1: a slice with at most one key per four bitmap words
+ *                   also sets a summary bitmap (one bit per non-empty word)
+ *                   and counts and emits only the non-empty words, clearing
+ *                   them behind; 0: every slice walks all its words.
  *   ms              measured time when tuned (output only). */
 typedef struct {
     int32_t path;
@@ -257,7 +279,7 @@ typedef struct {
     uint32_t persistent;
     uint32_t emit;
     uint32_t part_stream;
-    uint32_t reserved;
+    uint32_t summary;
     double ms;
 } bitsort_config_t;
 
@@ -282,6 +304,22 @@ bitsort_status_t bitsort_set_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max
 
 /* The configuration the context would use for (n, max_value). */
 bitsort_status_t bitsort_get_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max_value, bitsort_config_t *config);
+
+/* Batch policy of a context (used by plans created afterwards).  Arrays whose
+ * values fit one slice (max_value + 1 <= slice_values) are each sorted by one
+ * fused shared-memory slice; the others take `path` (BITSORT_PATH_PARTITION:
+ * high-bit partition + shared-memory slices; BITSORT_PATH_GLOBAL: global
+ * bitmap in L2) with slices of slice_values values.  Also used:
+ * block_threads (256/512), words_per_lane, stage; other fields ignored. */
+bitsort_status_t bitsort_set_batch_config(bitsort_ctx_t *ctx, const bitsort_config_t *config);
+bitsort_status_t bitsort_get_batch_config(bitsort_ctx_t *ctx, bitsort_config_t *config);
+
+/* Time candidate batch policies (path x slice size x block size x words per
+ * lane) on the given batch (device data; the outputs are overwritten) and
+ * keep the fastest as the context's batch policy, reported in *best
+ * (nullable).  Synchronises. */
+bitsort_status_t bitsort_batch_autotune(bitsort_ctx_t *ctx, const bitsort_desc_t *descs, size_t count,
+                                        bitsort_config_t *best);
 
 /* Save / load the tuned table as JSON text at `path`. */
 bitsort_status_t bitsort_tune_save(bitsort_ctx_t *ctx, const char *path);

@@ -31,13 +31,14 @@ PATH_NAMES = {0: "auto", 1: "fused", 2: "partition", 3: "global"}
 # names every build must export (checked by the CPU test-suite)
 EXPORTS = [
     "bitsort_ctx_create", "bitsort_ctx_destroy", "bitsort_status_string", "bitsort_last_error", "bitsort",
-    "bitsort_ex",
+    "bitsort_ex", "bitsort_i32",
     "bitsort_sync_status", "bitsort_batched", "bitsort_batch_plan_create", "bitsort_batch_plan_launch",
     "bitsort_batch_plan_results", "bitsort_batch_plan_device_results", "bitsort_batch_plan_destroy",
     "bitsort_server_create", "bitsort_server_submit", "bitsort_server_wait", "bitsort_server_stats",
     "bitsort_server_destroy", "bitsort_autotune", "bitsort_set_config", "bitsort_get_config",
     "bitsort_tune_save", "bitsort_tune_load", "bitsort_set_wait_limit_ms", "bitsort_debug_stalled_launch",
     "bitsort_kernel_launches", "bitsort_noalloc", "bitsort_set_phase_timing", "bitsort_phase_times",
+    "bitsort_set_batch_config", "bitsort_get_batch_config", "bitsort_batch_autotune",
 ]
 
 
@@ -55,13 +56,14 @@ class Config(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("slice_values", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("words_per_lane", ctypes.c_uint32), ("stage", ctypes.c_uint32), ("layout", ctypes.c_uint32),
                 ("persistent", ctypes.c_uint32), ("emit", ctypes.c_uint32), ("part_stream", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("ms", ctypes.c_double)]
+                ("summary", ctypes.c_uint32), ("ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"path": PATH_NAMES.get(self.path, self.path), "slice_values": self.slice_values,
                 "threads": self.block_threads, "words_per_lane": self.words_per_lane, "stage": self.stage,
                 "layout": LAYOUT_NAMES.get(self.layout, self.layout), "persistent": self.persistent,
-                "emit": EMIT_NAMES.get(self.emit, self.emit), "part_stream": self.part_stream, "ms": self.ms}
+                "emit": EMIT_NAMES.get(self.emit, self.emit), "part_stream": self.part_stream,
+                "summary": self.summary, "ms": self.ms}
 
 
 LAYOUT_EXACT, LAYOUT_CAPACITY = 0, 1
@@ -94,6 +96,7 @@ def _declare(lib):
         "bitsort_last_error": (ctypes.c_char_p, []),
         "bitsort": (st, [p, ctypes.c_size_t, u32, p, p]),
         "bitsort_ex": (st, [p, p, u64, u32, p, p, p]),
+        "bitsort_i32": (st, [p, p, u64, ctypes.c_int32, ctypes.c_int32, p, p, p]),
         "bitsort_sync_status": (st, [p, p, ctypes.POINTER(u64)]),
         "bitsort_batched": (st, [p, p, ctypes.c_size_t, p, p]),
         "bitsort_batch_plan_create": (st, [p, p, ctypes.c_size_t, ctypes.POINTER(p)]),
@@ -117,6 +120,9 @@ def _declare(lib):
         "bitsort_kernel_launches": (u64, [p]),
         "bitsort_noalloc": (st, [p, u64, u32, p, p, p]),
         "bitsort_set_phase_timing": (st, [p, i32]),
+        "bitsort_set_batch_config": (st, [p, ctypes.POINTER(Config)]),
+        "bitsort_get_batch_config": (st, [p, ctypes.POINTER(Config)]),
+        "bitsort_batch_autotune": (st, [p, p, ctypes.c_size_t, ctypes.POINTER(Config)]),
         "bitsort_phase_times": (st, [p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
                                      ctypes.POINTER(i32)]),
     }
@@ -204,6 +210,23 @@ class Context:
         _check(st, "bitsort_ex")
         return out
 
+    def sort_i32_async(self, keys, min_value: int, max_value: int, out=None, result=None, stream=None):
+        """Enqueue the sort of signed int32 `keys` in [min_value, max_value]; returns out."""
+        import torch
+        if out is None:
+            out = torch.empty_like(keys)
+        rptr = result.data_ptr() if result is not None else None
+        st = load().bitsort_i32(self.handle, _ptr(keys) if keys.numel() else None, keys.numel(), int(min_value),
+                                int(max_value), _ptr(out) if out.numel() else None, rptr, _stream_handle(stream))
+        _check(st, "bitsort_i32")
+        return out
+
+    def sort_i32(self, keys, min_value: int, max_value: int, out=None, stream=None):
+        """Signed sort and wait: returns (status, count, out)."""
+        out = self.sort_i32_async(keys, min_value, max_value, out=out, stream=stream)
+        st, cnt = self.sync_status(stream)
+        return st, cnt, out
+
     def sync_status(self, stream=None):
         cnt = ctypes.c_uint64(0)
         st = load().bitsort_sync_status(self.handle, _stream_handle(stream), ctypes.byref(cnt))
@@ -218,9 +241,9 @@ class Context:
     # tuning ----------------------------------------------------------------
     def set_config(self, n: int, max_value: int, path: int, slice_values: int = 0, threads: int = 0,
                    words_per_lane: int = 0, stage: int = 0, layout: int = LAYOUT_CAPACITY, persistent: int = 0,
-                   emit: int = EMIT_WORD, part_stream: int = 0):
-        cfg = Config(path, slice_values, threads, words_per_lane, stage, layout, persistent, emit, part_stream, 0,
-                     0.0)
+                   emit: int = EMIT_WORD, part_stream: int = 0, summary: int = 1):
+        cfg = Config(path, slice_values, threads, words_per_lane, stage, layout, persistent, emit, part_stream,
+                     summary, 0.0)
         _check(load().bitsort_set_config(self.handle, n, max_value, ctypes.byref(cfg)), "bitsort_set_config")
 
     def get_config(self, n: int, max_value: int):
@@ -276,6 +299,23 @@ class Context:
 
     def plan(self, arrays: Sequence) -> "BatchPlan":
         return BatchPlan(self, arrays)
+
+    def set_batch_config(self, path: int = PATH_PARTITION, slice_values: int = 0, threads: int = 0,
+                         words_per_lane: int = 0, stage: int = 0):
+        cfg = Config(path, slice_values, threads, words_per_lane, stage, 0, 1, 0, 0, 1, 0.0)
+        _check(load().bitsort_set_batch_config(self.handle, ctypes.byref(cfg)), "bitsort_set_batch_config")
+
+    def get_batch_config(self):
+        cfg = Config()
+        _check(load().bitsort_get_batch_config(self.handle, ctypes.byref(cfg)), "bitsort_get_batch_config")
+        return cfg.as_dict()
+
+    def batch_autotune(self, arrays: Sequence):
+        descs = _descs(arrays)
+        cfg = Config()
+        _check(load().bitsort_batch_autotune(self.handle, ctypes.byref(descs), len(arrays), ctypes.byref(cfg)),
+               "bitsort_batch_autotune")
+        return cfg.as_dict()
 
 
 def _descs(arrays):
@@ -386,6 +426,13 @@ def bitsort(keys, max_value: int, out=None, stream=None):
                         _ptr(out) if out.numel() else None, _stream_handle(stream))
     _check(st, "bitsort")
     return out
+
+
+def bitsort_i32(keys, min_value: int, max_value: int, out=None, stream=None):
+    """Enqueue the sort of signed int32 `keys` in [min_value, max_value]
+    through the C entry point `bitsort_i32` (per-device default context);
+    returns `out`.  Read the status with :func:`sync_status`."""
+    return default_context(keys.device.index).sort_i32_async(keys, min_value, max_value, out=out, stream=stream)
 
 
 def bitsort_noalloc(keys, max_value: int, out, result, stream=None):

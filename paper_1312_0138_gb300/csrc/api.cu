@@ -275,6 +275,7 @@ void bsx_describe(const bsx_config &cfg, const uint32_t *keys, uint32_t *out, ui
     a.cap = a.layout == LAYOUT_CAPACITY ? std::min<uint64_t>(cfg.S, n) : 0;
     a.emit = cfg.emit;
     a.stage_cap = bsx_stage_cap(cfg, n, M);
+    a.summary = (cfg.summary && cfg.path != BITSORT_PATH_GLOBAL) ? 1u : 0u;
     if (cfg.path == BITSORT_PATH_FUSED) {
         a.nslices = 1;
         a.key_tiles = 0;
@@ -369,13 +370,14 @@ static bsx_config fit_smem(const bitsort_ctx *c, bsx_config cfg, uint64_t n, uin
 
 static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, const uint32_t *keys, uint64_t n,
                                       uint64_t M, uint32_t *out, bitsort_result_t *d_result, cudaStream_t stream,
-                                      uint32_t stall) {
+                                      uint32_t stall, uint32_t bias = 0) {
     bsx_config cfg = fit_smem(c, bsx_sanitize(cfg0, n, M), n, M);
     EngineParams p;
     memset(&p, 0, sizeof(p));
     ArrayDesc &a = p.one;
     bsx_describe(cfg, keys, out, n, M, a);
     a.stall = stall;
+    a.bias = bias;
     bool alias = keys == out;
     if (cfg.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
         bitsort_status_t st = ensure_part(c, (uint64_t)a.nslices * a.cap);
@@ -511,6 +513,29 @@ extern "C" bitsort_status_t bitsort_ex(bitsort_ctx_t *c, const uint32_t *keys, u
     return launch_single(c, cfg, keys, n, M, out, d_result, s, 0);
 }
 
+extern "C" bitsort_status_t bitsort_i32(bitsort_ctx_t *c, const int32_t *keys, uint64_t n, int32_t min_value,
+                                        int32_t max_value, int32_t *out, bitsort_result_t *d_result,
+                                        bitsort_stream_t stream) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    if (min_value > max_value) return BITSORT_ERR_INVALID;
+    // x -> x - min_value (mod 2^32) maps [min_value, max_value] onto
+    // [0, max_value - min_value] in the same order: the unsigned sort of the
+    // shifted keys, with the shift undone on output
+    const uint32_t bias = (uint32_t)min_value;
+    const uint32_t span_max = (uint32_t)max_value - bias;
+    const uint32_t *k = reinterpret_cast<const uint32_t *>(keys);
+    uint32_t *o = reinterpret_cast<uint32_t *>(out);
+    bitsort_status_t st = bsx_validate(k, n, span_max, o);
+    if (st != BITSORT_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;
+    if (n == 0) return write_trivial_result(c, d_result, s);
+    const uint64_t M = (uint64_t)span_max + 1;
+    bsx_config cfg = bsx_lookup_config(c, n, M);
+    return launch_single(c, cfg, k, n, M, o, d_result, s, 0, bias);
+}
+
 extern "C" bitsort_status_t bitsort(const uint32_t *keys, size_t n, uint32_t max_value, uint32_t *out,
                                     bitsort_stream_t stream) {
     return bitsort_ex(nullptr, keys, (uint64_t)n, max_value, out, nullptr, stream);
@@ -604,7 +629,7 @@ static void to_public(const bsx_config &c, bitsort_config_t *o) {
     o->persistent = c.persistent ? 1 : 0;
     o->emit = c.emit;
     o->part_stream = c.stream_part ? 1 : 0;
-    o->reserved = 0;
+    o->summary = c.summary ? 1 : 0;
     o->ms = c.ms;
 }
 
@@ -630,6 +655,7 @@ extern "C" bitsort_status_t bitsort_set_config(bitsort_ctx_t *c, uint64_t n, uin
     cfg.persistent = in->persistent != 0;
     cfg.emit = in->emit;
     cfg.stream_part = in->part_stream != 0;
+    cfg.summary = in->summary != 0;
     c->table[key] = bsx_sanitize(cfg, n, M);
     return BITSORT_OK;
 }

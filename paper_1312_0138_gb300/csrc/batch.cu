@@ -20,6 +20,8 @@
 #include <new>
 #include <vector>
 
+#include <stdio.h>
+
 #include "engine.h"
 #include "internal.h"
 
@@ -52,34 +54,29 @@ struct bitsort_batch_plan {
     std::vector<bsx_config> cfg;
 };
 
-// Per-array configuration inside a batch: one slice when the whole bitmap
-// fits a CTA, else partition with the largest slice (fewest buckets, each
-// with enough keys to keep its CTA busy); a size class tuned on the context
-// overrides the path and slice size.
+// Per-array configuration inside a batch, from the context's batch policy:
+// an array whose values fit one slice (M <= policy.S) is sorted by one fused
+// slice; a larger one takes the policy's path (shared-memory slices after a
+// partition, or the global L2 bitmap) with slices of policy.S values.  One
+// persistent launch: every item waits for its own array's earlier phases;
+// exact bucket ranges, so the partition buffer is the output (or an n-entry
+// plan buffer when sorting in place).
 static bsx_config batch_config(bitsort_ctx *c, uint64_t n, uint64_t M, int threads) {
-    bsx_config cfg;
+    bsx_config cfg = c->batch;
     cfg.threads = threads;
-    // one persistent launch: every item waits for its own array's earlier
-    // phases; exact bucket ranges, so the partition buffer is the output (or
-    // an n-entry plan buffer when sorting in place)
     cfg.persistent = true;
     cfg.layout = LAYOUT_EXACT;
-    cfg.wpl = 1;
-    cfg.stage = false;
+    cfg.emit = EMIT_WORD;
     if (n == 0) {
         cfg.path = BITSORT_PATH_FUSED;
         cfg.S = 128;
         return cfg;
     }
-    if (M <= kFusedMaxM) {
-        cfg.path = BITSORT_PATH_FUSED;
-    } else {
-        cfg.path = BITSORT_PATH_PARTITION;
-        cfg.S = 1u << 20;
-    }
+    if (M <= std::min<uint64_t>(c->batch.S, kFusedMaxM)) cfg.path = BITSORT_PATH_FUSED;
     cfg = bsx_sanitize(cfg, n, M);
     cfg.persistent = true;
     cfg.layout = LAYOUT_EXACT;
+    cfg.emit = EMIT_WORD;
     return cfg;
 }
 
@@ -96,7 +93,7 @@ bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, siz
     if (!pl) return BITSORT_ERR_NOMEM;
     pl->ctx = c;
     pl->count = count;
-    pl->threads = 512;
+    pl->threads = c->batch.threads == 256 ? 256 : 512;
     pl->async_alloc = async_alloc;
     const int T = pl->threads;
 
@@ -361,4 +358,102 @@ extern "C" bitsort_status_t bitsort_batched(bitsort_ctx_t *c, const bitsort_desc
     st = bsx_plan_launch_direct(pl, s);
     bsx_plan_release_async(pl, s);
     return st;
+}
+
+// --------------------------------------------------------------- batch policy
+extern "C" bitsort_status_t bitsort_set_batch_config(bitsort_ctx_t *c, const bitsort_config_t *in) {
+    if (!c) c = bsx_default_ctx();
+    if (!c || !in) return BITSORT_ERR_INVALID;
+    if (in->path != BITSORT_PATH_PARTITION && in->path != BITSORT_PATH_GLOBAL) return BITSORT_ERR_INVALID;
+    bsx_config b = bitsort_ctx::batch_default();
+    b.path = (bitsort_path_t)in->path;
+    if (in->slice_values) b.S = std::max<uint32_t>(128, std::min<uint32_t>(in->slice_values, 1u << 20)) / 128 * 128;
+    if (in->block_threads) b.threads = in->block_threads == 256 ? 256 : 512;
+    if (in->words_per_lane) b.wpl = in->words_per_lane;
+    b.stage = in->stage != 0;
+    if (b.stage && b.wpl == 2) b.wpl = 1;
+    if (!b.stage && b.wpl == 8) b.wpl = 4;
+    if (b.wpl != 1 && b.wpl != 2 && b.wpl != 4 && b.wpl != 8) b.wpl = 1;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->batch = b;
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_get_batch_config(bitsort_ctx_t *c, bitsort_config_t *out) {
+    if (!c) c = bsx_default_ctx();
+    if (!c || !out) return BITSORT_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    memset(out, 0, sizeof(*out));
+    out->path = (int32_t)c->batch.path;
+    out->slice_values = c->batch.S;
+    out->block_threads = (uint32_t)c->batch.threads;
+    out->words_per_lane = c->batch.wpl;
+    out->stage = c->batch.stage ? 1 : 0;
+    out->persistent = 1;
+    out->ms = c->batch.ms;
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_batch_autotune(bitsort_ctx_t *c, const bitsort_desc_t *descs, size_t count,
+                                                   bitsort_config_t *best_out) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;
+    const bsx_config saved = c->batch;
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return BITSORT_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    bsx_config best_cfg = saved;
+    for (int path : {(int)BITSORT_PATH_PARTITION, (int)BITSORT_PATH_GLOBAL}) {
+        for (uint32_t S : {1u << 17, 1u << 18, 1u << 19, 1u << 20}) {
+            for (int T : {256, 512}) {
+                for (uint32_t wpl : {1u, 2u}) {
+                    bsx_config b = bitsort_ctx::batch_default();
+                    b.path = (bitsort_path_t)path;
+                    b.S = S;
+                    b.threads = T;
+                    b.wpl = wpl;
+                    c->batch = b;
+                    bitsort_batch_plan *pl = nullptr;
+                    if (bsx_plan_build(c, descs, count, nullptr, nullptr, false, &pl) != BITSORT_OK) continue;
+                    bool ok = bsx_plan_launch_direct(pl, s) == BITSORT_OK;   // warm-up
+                    float ms = 0, sum = 0;
+                    for (int r = 0; r < 3 && ok; ++r) {
+                        cudaEventRecord(e0, s);
+                        ok = bsx_plan_launch_direct(pl, s) == BITSORT_OK;
+                        cudaEventRecord(e1, s);
+                        if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        sum += ms;
+                    }
+                    std::vector<bitsort_result_t> res(count);
+                    bitsort_status_t st = bitsort_batch_plan_results(pl, s, res.data());
+                    bitsort_batch_plan_destroy(pl);
+                    if (!ok || st == BITSORT_ERR_TIMEOUT || st == BITSORT_ERR_CUDA) continue;
+                    const double mean = sum / 3.0;
+                    if (mean < best) {
+                        best = mean;
+                        best_cfg = b;
+                    }
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (best >= 1e30) {
+        c->batch = saved;
+        return BITSORT_ERR_CUDA;
+    }
+    best_cfg.ms = best;
+    c->batch = best_cfg;
+    if (best_out) {
+        bitsort_get_batch_config(c, best_out);
+        best_out->ms = best;
+    }
+    return BITSORT_OK;
 }

@@ -95,6 +95,8 @@ struct SharedMisc {
     uint32_t ticket;
     uint32_t flag;
     uint32_t total;
+    uint32_t summ_clean;   // the summary bitmap (start of shared memory) is all zero
+    uint32_t bm_clean_w;   // the slice bitmap's first bm_clean_w words are zero
 };
 
 // Thread 0 only: wait until *p >= target.  Gives up (false) when the array's
@@ -577,15 +579,18 @@ __device__ void slice_lookback(const EngineParams &P, const ArrayDesc &a, uint32
 // returns the array's scratch to its zero state for the next launch.
 template <int T>
 __device__ void slice_complete(const ArrayDesc &a, SharedMisc &m) {
-    __threadfence();
+    // the barrier orders the block's writes before thread 0's fence, which
+    // makes them visible device-wide before the completion count (and, for
+    // the last CTA, the count before its reads)
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         const uint32_t d = atomicAdd(&a.sync[SY_SLICES_DONE], 1u);
         m.flag = (d == a.nslices - 1) ? 1u : 0u;
+        if (m.flag) __threadfence();
     }
     __syncthreads();
     if (m.flag) {
-        __threadfence();
         uint64_t total = m.total;
         if (a.nslices > 1) total = ld_acquire_u64(&a.look[a.nslices - 1]) & LB_VALUE;
         __syncthreads();
@@ -639,8 +644,10 @@ __device__ void hist_range(const ArrayDesc &a, uint64_t lo, uint64_t hi, uint32_
     __syncthreads();
     bool bad = false;
     const uint64_t M = a.M, magic = a.div_magic;
+    const uint32_t bias = a.bias;
     for_each_key<T, false>(a.keys, lo, hi, [&](uint32_t x) {
-        if ((uint64_t)x < M) atomicAdd(&hist[bucket_of(x, magic)], 1u);
+        const uint32_t y = x - bias;
+        if ((uint64_t)y < M) atomicAdd(&hist[bucket_of(y, magic)], 1u);
         else bad = true;
     });
     bad = __syncthreads_or(bad);
@@ -649,21 +656,23 @@ __device__ void hist_range(const ArrayDesc &a, uint64_t lo, uint64_t hi, uint32_
         const uint32_t c = hist[i];
         if (c) atomicAdd(&a.counts[i], c);
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         const uint32_t d = atomicAdd(&a.sync[SY_HIST_DONE], 1u);
         m.flag = (d == expected - 1) ? 1u : 0u;
+        if (m.flag) __threadfence();
     }
     __syncthreads();
     if (m.flag) {
-        __threadfence();
         block_exclusive_scan<T>(
             nb, [&](uint32_t i) -> uint64_t { return __ldcg(&a.counts[i]); },
             [&](uint32_t i, uint64_t v) { a.offsets[i] = v; }, m);
-        __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) st_release_u32(&a.sync[SY_OFFSETS_READY], 1u);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_u32(&a.sync[SY_OFFSETS_READY], 1u);
+        }
     }
 }
 
@@ -695,14 +704,16 @@ __device__ void part_tile(const ArrayDesc &a, const uint32_t (&x)[kKeysPerThread
     const bool capacity = a.layout == LAYOUT_CAPACITY;
     const uint64_t magic = a.div_magic;
     const uint32_t maxv = (uint32_t)(a.M - 1);
+    const uint32_t bias = a.bias;   // keys are classified as x - bias; the buffer keeps x
     uint32_t br[K];   // bin << 16 | rank in the tile
     bool bad = false;
     if (nkeys == (uint32_t)a.tile_keys) {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const bool in = x[j] <= maxv;
+            const uint32_t y = x[j] - bias;
+            const bool in = y <= maxv;
             bad |= !in;
-            const uint32_t bin = in ? bucket_of(x[j], magic) : nb;
+            const uint32_t bin = in ? bucket_of(y, magic) : nb;
             br[j] = (bin << 16) | atomicAdd(&hist[bin], 1u);
         }
     } else {
@@ -710,9 +721,10 @@ __device__ void part_tile(const ArrayDesc &a, const uint32_t (&x)[kKeysPerThread
         for (int j = 0; j < K; ++j) {
             br[j] = 0xFFFFFFFFu;
             if ((uint32_t)j * T + threadIdx.x < nkeys) {
-                const bool in = x[j] <= maxv;
+                const uint32_t y = x[j] - bias;
+                const bool in = y <= maxv;
                 bad |= !in;
-                const uint32_t bin = in ? bucket_of(x[j], magic) : nb;
+                const uint32_t bin = in ? bucket_of(y, magic) : nb;
                 br[j] = (bin << 16) | atomicAdd(&hist[bin], 1u);
             }
         }
@@ -814,9 +826,11 @@ __device__ void item_part(const EngineParams &P, const ArrayDesc &a, uint32_t ti
         part_tile<T>(a, x, nkeys, hist, delta, lim, sorted, sorted_b, m);
     }
     if (!a.phased) {
-        __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(&a.sync[SY_PART_DONE], 1u);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&a.sync[SY_PART_DONE], 1u);
+        }
     }
 }
 
@@ -961,6 +975,70 @@ __device__ void part_stream(const EngineParams &P, const ArrayDesc &a, char *sme
     if (pend1) mbar_wait(&mbar[1], uses1 & 1u, P.wait_limit_ns);
 }
 
+// Sparse slice (few keys for its words): the scatter also set one summary
+// bit per non-empty word (summ), so counting and emission visit only the
+// non-empty words: a lane takes one summary word (32 bitmap words) per step.
+// Every word read is cleared behind (bitmap and summary), so the slice is zero
+// again for this CTA's next sparse slice without a full clear.
+template <int T>
+__device__ void slice_finish_sparse(const EngineParams &P, const ArrayDesc &a, uint32_t s, uint32_t *bm,
+                                    uint32_t *summ, uint32_t words, uint32_t v0, SharedMisc &m) {
+    constexpr int NW = T / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nsw = (words + 31) / 32;
+    const uint32_t spw = (((nsw + NW - 1) / NW) + 31u) & ~31u;
+    const uint32_t s0 = min(nsw, (uint32_t)warp * spw), s1 = min(nsw, s0 + spw);
+    uint32_t cnt = 0;
+    for (uint32_t j = s0 + lane; j < s1; j += 32) {
+        uint32_t sm = summ[j];
+        while (sm) {
+            cnt += __popc(bm[j * 32 + (__ffs(sm) - 1)]);
+            sm &= sm - 1;
+        }
+    }
+    cnt = warp_sum_u32(cnt);
+    if (lane == 0) m.wcount[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t c = lane < NW ? m.wcount[lane] : 0;
+        const uint32_t incl = warp_incl_scan_u32(c, lane);
+        if (lane < NW) m.wbase[lane] = incl - c;
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const uint64_t excl = a.nslices > 1 ? lookback(P, a, s, total, lane) : 0;
+        if (lane == 0) {
+            m.excl = excl;
+            m.total = total;
+        }
+    }
+    __syncthreads();
+    uint64_t base = m.excl + m.wbase[warp];
+    const uint64_t lim = a.n;
+    uint32_t *out = a.out;
+    for (uint32_t j0 = s0; j0 < s1; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const uint32_t sm0 = j < s1 ? summ[j] : 0u;
+        uint32_t c = 0;
+        for (uint32_t sm = sm0; sm; sm &= sm - 1) c += __popc(bm[j * 32 + (__ffs(sm) - 1)]);
+        const uint32_t incl = warp_incl_scan_u32(c, lane);
+        const uint32_t chunk = __shfl_sync(kFull, incl, 31);
+        uint64_t o = base + incl - c;
+        for (uint32_t sm = sm0; sm; sm &= sm - 1) {
+            const uint32_t w = j * 32 + (__ffs(sm) - 1);
+            uint32_t x = bm[w];
+            bm[w] = 0u;
+            const uint32_t val = v0 + w * 32u - 1u;
+            while (x) {
+                if (o < lim) __stcs(out + o, val + __ffs(x));   // never past n
+                ++o;
+                x &= x - 1;
+            }
+        }
+        if (sm0) summ[j] = 0u;
+        base += chunk;
+    }
+    slice_complete<T>(a, m);
+}
+
 template <int T>
 __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t b, char *smem, SharedMisc &m) {
     constexpr int NW = T / 32;
@@ -969,8 +1047,10 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     const uint64_t vals = min((uint64_t)a.S, a.M - v0);
     const uint32_t words = (uint32_t)((vals + 31) >> 5);
     const uint32_t w4 = (words + 3u) & ~3u;
-    // shared memory: EMIT_WORD [stage (optional) | bitmap]; EMIT_RANK [bitmap | prefix | outputs]
-    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
+    // shared memory: [summary bitmap] then EMIT_WORD [stage (optional) | bitmap]
+    // or EMIT_RANK [bitmap | prefix | outputs]
+    uint32_t *summ = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *stage = summ + kSummaryWords;
     uint32_t *bm = (!rank && a.stage) ? stage + NW * kStageWords : stage;
     uint32_t *pre = bm + w4;
     uint32_t *outs = pre + w4;
@@ -982,8 +1062,6 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
             m.flag = wait_geq(&a.sync[SY_PART_DONE], a.key_tiles + a.stall, &a.sync[SY_TIMEOUT], P.wait_limit_ns)
                          ? 1u : 0u;
     }
-    uint4 *bm4 = reinterpret_cast<uint4 *>(bm);
-    for (uint32_t i = threadIdx.x; i < w4 / 4; i += T) bm4[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
 
     // where the slice's keys are: a range of the partition buffer, or the
@@ -1003,32 +1081,69 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
         lo = min(__ldcg(&a.offsets[b]), a.n);
         hi = lo + min((uint64_t)__ldcg(&a.counts[b]), a.n - lo);
     }
-    const uint32_t base = (uint32_t)v0, span = (uint32_t)vals;
+    if (!m.flag) hi = lo;
+    // sparse slice: at most one key per four bitmap words (summary bitmap)
+    const bool sparse = !rank && a.summary && (hi - lo) * 4 <= (uint64_t)words;
+    if (!m.summ_clean) {
+        for (uint32_t i = threadIdx.x; i < kSummaryWords; i += T) summ[i] = 0u;
+    }
+    if (!sparse || m.bm_clean_w < w4) {
+        uint4 *bm4 = reinterpret_cast<uint4 *>(bm);
+        for (uint32_t i = threadIdx.x; i < w4 / 4; i += T) bm4[i] = make_uint4(0, 0, 0, 0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) m.summ_clean = 1u;
+
+    const uint32_t bias = a.bias;
+    const uint32_t base = (uint32_t)v0 + bias, span = (uint32_t)vals;   // slice values: x - base in [0, span)
     bool bad = false;
-    if (m.flag) {
+    if (sparse) {
+        auto set_bits = [&](uint32_t l) {
+            const uint32_t w = l >> 5;
+            atomicOr(&bm[w], 1u << (l & 31));
+            atomicOr(&summ[w >> 5], 1u << (w & 31));
+        };
         if (filter_range) {
             const uint64_t M = a.M;
             for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
-                if ((uint64_t)x < M) atomicOr(&bm[x >> 5], 1u << (x & 31));
+                const uint32_t y = x - bias;
+                if ((uint64_t)y < M) set_bits(y);
                 else bad = true;
             });
         } else {
             for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
                 const uint32_t l = x - base;
-                if (l < span) atomicOr(&bm[l >> 5], 1u << (l & 31));
+                if (l < span) set_bits(l);
             });
         }
-    } else if (threadIdx.x == 0) {
-        atomicOr(&a.sync[SY_TIMEOUT], 1u);
+    } else if (filter_range) {
+        const uint64_t M = a.M;
+        for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
+            const uint32_t y = x - bias;
+            if ((uint64_t)y < M) atomicOr(&bm[y >> 5], 1u << (y & 31));
+            else bad = true;
+        });
+    } else {
+        for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
+            const uint32_t l = x - base;
+            if (l < span) atomicOr(&bm[l >> 5], 1u << (l & 31));
+        });
     }
+    if (!m.flag && threadIdx.x == 0) atomicOr(&a.sync[SY_TIMEOUT], 1u);
     bad = __syncthreads_or(bad);
     if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
     if (partitioned && threadIdx.x == 0) {
         a.counts[b] = 0;
         a.cursor[b] = 0;
     }
+    if (sparse) {
+        slice_finish_sparse<T>(P, a, b, bm, summ, words, base, m);
+        if (threadIdx.x == 0) m.bm_clean_w = max(m.bm_clean_w, w4);   // every word read was cleared
+        return;
+    }
+    if (threadIdx.x == 0) m.bm_clean_w = 0u;
     if (!rank) {
-        slice_finish<T>(P, a, b, bm, words, (uint32_t)v0, stage, m);
+        slice_finish<T>(P, a, b, bm, words, base, stage, m);
         return;
     }
 
@@ -1044,7 +1159,7 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     if (total > a.stage_cap) {
         // more outputs than the staging room (skewed keys): walk the words instead
         slice_lookback<T>(P, a, b, m);
-        emit_words<1>(bm, w0, w1, (uint32_t)v0, m.excl + m.wbase[warp], a.out, a.n);
+        emit_words<1>(bm, w0, w1, base, m.excl + m.wbase[warp], a.out, a.n);
         slice_complete<T>(a, m);
         return;
     }
@@ -1063,9 +1178,10 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     if (filter_range) {
         const uint64_t M = a.M;
         for_each_key<T, true>(src, lo, hi, [&](uint32_t x) {
-            if ((uint64_t)x < M) {
-                const uint32_t w = x >> 5;
-                outs[pre[w] + __popc(bm[w] & ((1u << (x & 31)) - 1u))] = x;
+            const uint32_t y = x - bias;
+            if ((uint64_t)y < M) {
+                const uint32_t w = y >> 5;
+                outs[pre[w] + __popc(bm[w] & ((1u << (y & 31)) - 1u))] = x;
             }
         });
     } else {
@@ -1094,8 +1210,10 @@ __device__ void gscatter_range(const ArrayDesc &a, uint64_t lo, uint64_t hi) {
     const uint64_t M = a.M;
     uint32_t *bitmap = a.bitmap;
     bool bad = false;
+    const uint32_t bias = a.bias;
     for_each_key<T, true>(a.keys, lo, hi, [&](uint32_t x) {
-        if ((uint64_t)x < M) atomicOr(&bitmap[x >> 5], 1u << (x & 31));
+        const uint32_t y = x - bias;
+        if ((uint64_t)y < M) atomicOr(&bitmap[y >> 5], 1u << (y & 31));
         else bad = true;
     });
     bad = __syncthreads_or(bad);
@@ -1106,15 +1224,17 @@ template <int T>
 __device__ void item_gscatter(const EngineParams &P, const ArrayDesc &a, uint32_t tile, SharedMisc &m) {
     const uint64_t lo = (uint64_t)tile * a.tile_keys;
     gscatter_range<T>(a, lo, min(lo + a.tile_keys, a.n));
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(&a.sync[SY_PART_DONE], 1u);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&a.sync[SY_PART_DONE], 1u);
+    }
 }
 
 template <int T>
 __device__ void item_gscan(const EngineParams &P, const ArrayDesc &a, uint32_t s, char *smem, SharedMisc &m) {
     constexpr int NW = T / 32;
-    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem) + kSummaryWords;
     uint32_t *bm = a.stage ? stage + NW * kStageWords : stage;
     const uint64_t v0 = (uint64_t)s * a.S;
     const uint64_t vals = min((uint64_t)a.S, a.M - v0);
@@ -1140,7 +1260,7 @@ __device__ void item_gscan(const EngineParams &P, const ArrayDesc &a, uint32_t s
     }
     __syncthreads();
     // words past the array's last value are zero in the bitmap (padding)
-    slice_finish<T>(P, a, s, bm, words, (uint32_t)v0, stage, m);
+    slice_finish<T>(P, a, s, bm, words, (uint32_t)v0 + a.bias, stage, m);
 }
 
 // ----------------------------------------------------------------- kernel
@@ -1149,6 +1269,10 @@ __global__ void __launch_bounds__(T, 1024 / T) engine_kernel(const __grid_consta
     extern __shared__ __align__(16) char smem[];
     __shared__ SharedMisc m;
     const Segment *segs = P.segments ? P.segments : P.seg;
+    if (threadIdx.x == 0) {
+        m.summ_clean = 0u;
+        m.bm_clean_w = 0u;
+    }
     for (;;) {
         if (threadIdx.x == 0) m.ticket = atomicAdd(&P.ticket[0], 1u);
         __syncthreads();
@@ -1173,6 +1297,11 @@ __global__ void __launch_bounds__(T, 1024 / T) engine_kernel(const __grid_consta
             default: break;
         }
         __syncthreads();
+        if (threadIdx.x == 0 && sg.type != IT_BUCKET) {
+            // other items use the shared memory their own way
+            m.bm_clean_w = 0u;
+            if (sg.type != IT_GSCAN) m.summ_clean = 0u;
+        }
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -1200,6 +1329,10 @@ template <int T, int TYPE>
 __global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constant__ EngineParams P) {
     extern __shared__ __align__(16) char smem[];
     __shared__ SharedMisc m;
+    if (threadIdx.x == 0) {
+        m.summ_clean = 0u;
+        m.bm_clean_w = 0u;
+    }
     pdl_wait();
     const ArrayDesc &a = P.one;
     if constexpr (TYPE == IT_BUCKET || TYPE == IT_GSCAN) {

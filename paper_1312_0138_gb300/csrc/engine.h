@@ -76,6 +76,9 @@ struct __align__(16) ArrayDesc {
     uint32_t phased;            // 1: phases are separate kernels (ordered by the stream)
     uint32_t emit;              // EMIT_WORD or EMIT_RANK (BUCKET items)
     uint32_t stage_cap;         // EMIT_RANK: outputs a slice may stage in shared memory
+    uint32_t summary;           // 1: sparse slices keep a summary bitmap (one bit per word)
+    uint32_t bias;              // keys are classified as x - bias (mod 2^32); outputs get it back
+    uint32_t pad_[2];
 };
 
 // How a BUCKET item turns its bitmap slice into output positions.
@@ -120,17 +123,20 @@ struct EngineParams {
 };
 
 // Shared-memory sizes (bytes) an item type needs for a given configuration.
+// Slice items start with a summary bitmap of kSummaryWords words (one bit per
+// bitmap word of a slice of up to 2^20 values), used by sparse slices.
+constexpr uint32_t kSummaryWords = 1024;
 constexpr uint32_t kStageWords = 1024 + 4;  // per warp: staged positions (+ room for the 16-byte alignment shift)
 inline uint32_t slice_smem_bytes(uint32_t S, int threads, bool stage) {
     uint32_t words = (S + 31) / 32;
     uint32_t w4 = (words + 3) & ~3u;
-    return w4 * 4 + (stage ? (uint32_t)(threads / 32) * kStageWords * 4 : 0u);
+    return kSummaryWords * 4 + w4 * 4 + (stage ? (uint32_t)(threads / 32) * kStageWords * 4 : 0u);
 }
 // EMIT_RANK: bitmap + per-word prefix + staged outputs
 inline uint32_t rank_smem_bytes(uint32_t S, uint32_t stage_cap) {
     uint32_t words = (S + 31) / 32;
     uint32_t w4 = (words + 3) & ~3u;
-    return w4 * 8 + ((stage_cap + 3) & ~3u) * 4;
+    return kSummaryWords * 4 + w4 * 8 + ((stage_cap + 3) & ~3u) * 4;
 }
 // PART: per bucket (plus one discard bin) count, delta, limit; the tile and its bucket tags
 inline uint32_t part_smem_bytes(uint32_t nslices, uint32_t tile_keys) {

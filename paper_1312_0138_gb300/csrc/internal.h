@@ -22,6 +22,7 @@ struct bsx_config {
     uint32_t wpl = 2;        // bitmap words per lane in the scan (1, 2, 4)
     bool stage = false;      // stage set-bit positions per warp in shared memory
     uint32_t emit = 0;       // bsx::EMIT_WORD (0) or bsx::EMIT_RANK (1)
+    bool summary = true;     // sparse slices keep a summary bitmap (word emission)
     bool stream_part = false; // phased PARTITION: stream tiles through bulk copies when keys are 16-byte aligned
     double ms = 0;           // measured time when tuned (0 = not measured)
 };
@@ -60,6 +61,21 @@ struct bitsort_ctx {
 
     std::mutex mu;
     std::map<std::pair<int, int>, bsx_config> table;  // (ceil log2 n, ceil log2 M) -> config
+    // policy of batched launches: arrays with M <= batch.S are one fused
+    // slice, the others take batch.path with slices of batch.S values
+    bsx_config batch = batch_default();
+
+    static bsx_config batch_default() {
+        bsx_config b;
+        b.path = BITSORT_PATH_PARTITION;
+        b.S = 1u << 19;
+        b.threads = 512;
+        b.wpl = 1;
+        b.stage = false;
+        b.persistent = true;
+        b.layout = 0;
+        return b;
+    }
     std::atomic<uint64_t> launches{0};
 };
 

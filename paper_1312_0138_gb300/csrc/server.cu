@@ -5,10 +5,12 @@
 //   * requests wait in arrival order; the head request is admitted while the
 //     bytes its bitmap and output need, ceil(M/8) + 4n, fit in what is left of
 //     the budget (strict FIFO, so a large request is never starved);
-//   * whenever one of `max_inflight` slots (a stream each) is free and
-//     admitted requests are waiting, they are launched together as one batch
-//     (one persistent engine launch) on that slot's stream, so batches that
-//     are launched while others run overlap on the device;
+//   * whenever one of `max_inflight` slots (a stream and a context each) is
+//     free and admitted requests are waiting, they are launched on that
+//     slot's stream: requests of at least kPlainMinKeys keys each as one
+//     plain sort (one kernel per phase, every SM), the smaller ones together
+//     as one batch (one persistent launch); work launched while other slots
+//     run overlaps with it on the device;
 //   * a finished batch (its event has completed) releases its budget, and its
 //     requests' outcomes (copied to pinned host memory behind the kernel) are
 //     handed to the waiters together with their latency, measured from
@@ -16,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -48,6 +51,8 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    bitsort_ctx *ctx = nullptr;                // scratch of this slot's plain sorts
+    bitsort_result_t *dev_results = nullptr;   // kMaxBatch outcomes on the device
     bitsort_result_t *host_results = nullptr;  // pinned
     size_t host_cap = 0;
     bool busy = false;
@@ -56,6 +61,7 @@ struct Slot {
 };
 
 constexpr size_t kMaxBatch = 1024;
+constexpr uint64_t kPlainMinKeys = 1ull << 20;   // requests this large run as plain sorts
 
 uint64_t request_bytes(uint64_t n, uint32_t max_value) {
     const uint64_t M = (uint64_t)max_value + 1;
@@ -86,29 +92,40 @@ struct bitsort_server {
 };
 
 bool bitsort_server::launch_batch(Slot &s, std::vector<uint64_t> &batch) {
-    std::vector<bitsort_desc_t> descs(batch.size());
-    for (size_t i = 0; i < batch.size(); ++i) {
-        const Request &r = reqs[batch[i]];
-        descs[i].keys = r.keys;
-        descs[i].out = r.out;
-        descs[i].n = r.n;
-        descs[i].max_value = r.max_value;
-        descs[i].reserved = 0;
-    }
-    if (s.host_cap < batch.size()) {
-        if (s.host_results) cudaFreeHost(s.host_results);
-        s.host_results = nullptr;
-        s.host_cap = 0;
+    if (!s.host_results) {
         if (cudaMallocHost(&s.host_results, kMaxBatch * sizeof(bitsort_result_t)) != cudaSuccess) return false;
         s.host_cap = kMaxBatch;
     }
-    bitsort_batch_plan *pl = nullptr;
-    bitsort_status_t st = bsx_plan_build(ctx, descs.data(), descs.size(), nullptr, s.stream, true, &pl);
-    if (st != BITSORT_OK) return false;
-    st = bsx_plan_launch_direct(pl, s.stream);
-    cudaMemcpyAsync(s.host_results, bsx_plan_results_ptr(pl), batch.size() * sizeof(bitsort_result_t),
-                    cudaMemcpyDeviceToHost, s.stream);
-    bsx_plan_release_async(pl, s.stream);
+    // large requests first (plain sorts), then the small ones (one batch);
+    // outcome i of the slot belongs to ticket i of the reordered list
+    std::stable_partition(batch.begin(), batch.end(), [&](uint64_t t) { return reqs[t].n >= kPlainMinKeys; });
+    size_t nplain = 0;
+    while (nplain < batch.size() && reqs[batch[nplain]].n >= kPlainMinKeys) ++nplain;
+    bitsort_status_t st = BITSORT_OK;
+    if (nplain < batch.size()) {
+        std::vector<bitsort_desc_t> descs(batch.size() - nplain);
+        for (size_t i = nplain; i < batch.size(); ++i) {
+            const Request &r = reqs[batch[i]];
+            bitsort_desc_t &d = descs[i - nplain];
+            d.keys = r.keys;
+            d.out = r.out;
+            d.n = r.n;
+            d.max_value = r.max_value;
+            d.reserved = 0;
+        }
+        bitsort_batch_plan *pl = nullptr;
+        st = bsx_plan_build(ctx, descs.data(), descs.size(), s.dev_results + nplain, s.stream, true, &pl);
+        if (st != BITSORT_OK) return false;
+        st = bsx_plan_launch_direct(pl, s.stream);
+        bsx_plan_release_async(pl, s.stream);
+    }
+    for (size_t i = 0; i < nplain && st == BITSORT_OK; ++i) {
+        const Request &r = reqs[batch[i]];
+        st = bitsort_ex(s.ctx, r.keys, r.n, r.max_value, r.out, s.dev_results + i,
+                        reinterpret_cast<bitsort_stream_t>(s.stream));
+    }
+    cudaMemcpyAsync(s.host_results, s.dev_results, batch.size() * sizeof(bitsort_result_t), cudaMemcpyDeviceToHost,
+                    s.stream);
     cudaEventRecord(s.done, s.stream);
     s.tickets = batch;
     s.busy = true;
@@ -148,10 +165,16 @@ void bitsort_server::run() {
             busy += s.busy ? 1 : 0;
         }
         if (progressed) cv_done.notify_all();
+        size_t free_slots = 0;
+        for (Slot &s : slots) free_slots += s.busy ? 0 : 1;
         for (Slot &s : slots) {
             if (s.busy || waiting.empty()) continue;
+            // an even share of the waiting requests per free slot, so that a
+            // burst spreads over the slots and overlaps on the device
+            const size_t share = std::min(kMaxBatch, (waiting.size() + free_slots - 1) / std::max<size_t>(1, free_slots));
+            --free_slots;
             std::vector<uint64_t> batch;
-            while (!waiting.empty() && batch.size() < kMaxBatch) {
+            while (!waiting.empty() && batch.size() < share) {
                 Request &r = reqs[waiting.front()];
                 if (in_use + r.bytes > budget) break;
                 in_use += r.bytes;
@@ -204,7 +227,9 @@ extern "C" bitsort_status_t bitsort_server_create(int device, uint64_t budget_by
     sv->slots.resize(max_inflight);
     for (Slot &s : sv->slots) {
         if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
+            bitsort_ctx_create(device, &s.ctx) != BITSORT_OK ||
+            cudaMalloc(&s.dev_results, kMaxBatch * sizeof(bitsort_result_t)) != cudaSuccess) {
             bitsort_server_destroy(sv);
             return BITSORT_ERR_CUDA;
         }
@@ -278,6 +303,8 @@ extern "C" bitsort_status_t bitsort_server_destroy(bitsort_server_t *sv) {
         if (s.done) cudaEventDestroy(s.done);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.host_results) cudaFreeHost(s.host_results);
+        if (s.dev_results) cudaFree(s.dev_results);
+        if (s.ctx) bitsort_ctx_destroy(s.ctx);
     }
     if (sv->ctx) bitsort_ctx_destroy(sv->ctx);
     delete sv;

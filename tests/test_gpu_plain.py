@@ -223,3 +223,34 @@ def test_autotune_picks_a_correct_config(ctx, tmp_path):
     a2, a1 = c2.get_config(1 << 18, (1 << 22) - 1), ctx.get_config(1 << 18, (1 << 22) - 1)
     assert {k: a2[k] for k in a2 if k != "ms"} == {k: a1[k] for k in a1 if k != "ms"}
     c2.close()
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("summary", [0, 1])
+def test_sparse_slices_summary_bitmap(ctx, layout, summary):
+    # 16 slices of 2^20 values with ~190 keys each: sparse (summary bitmap)
+    keys = gen.floyd(41, 3000, 1 << 24)
+    check(ctx, keys, (1 << 24) - 1, path=bs.PATH_PARTITION, S=1 << 20, layout=layout, summary=summary)
+    # a full 32-bit range with few keys
+    keys = gen.feistel(42, 20_000, 1 << 32)
+    check(ctx, keys, (1 << 32) - 1, path=bs.PATH_PARTITION, S=1 << 20, layout=layout, summary=summary)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_sparse_and_dense_slices_mixed(ctx, persistent):
+    # dense lower half, a sprinkle of keys in the upper half: the CTAs meet
+    # dense and sparse slices in turn (the cleared-bitmap bookkeeping)
+    lo = gen.floyd(43, 400_000, 1 << 20)
+    hi = (gen.floyd(44, 300, 1 << 23) + (1 << 23)).astype(np.uint32)
+    keys = gen.shuffle(45, np.concatenate([lo, hi]))
+    for S in (1 << 16, 1 << 18):
+        check(ctx, keys, (1 << 24) - 1, path=bs.PATH_PARTITION, S=S, layout=1, persistent=persistent)
+    check(ctx, keys, (1 << 24) - 1, path=bs.PATH_PARTITION, S=1 << 17, layout=0, threads=256)
+
+
+def test_sparse_duplicates_and_in_place(ctx):
+    keys = gen.uniform_with_replacement(46, 2000, 1 << 24)
+    check(ctx, keys, (1 << 24) - 1, path=bs.PATH_PARTITION, S=1 << 20, layout=1)
+    keys = gen.floyd(47, 2500, 1 << 22)
+    check(ctx, keys, (1 << 22) - 1, path=bs.PATH_PARTITION, S=1 << 20, layout=1, inplace=True)
+    check(ctx, gen.floyd(48, 5000, 1 << 20), (1 << 20) - 1, path=bs.PATH_FUSED)   # fused, sparse
