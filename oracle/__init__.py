@@ -59,6 +59,8 @@ def bind(path: str):
     lib.oracle_bitmap_sort_i32.argtypes = [p, u64, ctypes.c_int32, ctypes.c_int32, p,
                                            ctypes.POINTER(u64)]
     lib.oracle_bitmap_sort_i32.restype = ctypes.c_int
+    lib.oracle_bitmap_sort_u64.argtypes = [p, u64, u64, p, ctypes.POINTER(u64)]
+    lib.oracle_bitmap_sort_u64.restype = ctypes.c_int
     return lib
 
 
@@ -121,6 +123,17 @@ class Oracle:
                                              int(max_value), out.ctypes.data, ctypes.byref(count))
         if st < 0 or st == NOMEM:
             raise ValueError("oracle_bitmap_sort_i32 failed")
+        return st, out[:count.value].copy()
+
+    def bitmap_sort_u64(self, keys, max_value: int):
+        """Bitmap sort of 64-bit keys bounded by max_value (< 2^40)."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        out = np.empty(max(keys.size, 1), dtype=np.uint64)
+        count = ctypes.c_uint64(0)
+        st = self.lib.oracle_bitmap_sort_u64(keys.ctypes.data, keys.size, int(max_value), out.ctypes.data,
+                                             ctypes.byref(count))
+        if st < 0 or st == NOMEM:
+            raise ValueError("oracle_bitmap_sort_u64 failed")
         return st, out[:count.value].copy()
 
     def batched(self, arrays):

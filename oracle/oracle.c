@@ -30,6 +30,10 @@
  *                         non-negatives separated (order kept), each sorted
  *                         by the first function over bits 0..t-2, negatives
  *                         written first.
+ *   oracle_bitmap_sort_i32  the bit-set form for signed keys in
+ *                         [min_value, max_value] (offsets from min_value).
+ *   oracle_bitmap_sort_u64  the bit-set form for 64-bit keys (Algorithm 1 is
+ *                         written for any integer type T).
  *
  * Status codes (same numbering as the GPU library's public header, written
  * out again here on purpose):
@@ -187,4 +191,38 @@ int oracle_bitmap_sort_i32(const int32_t *keys, uint64_t n, int32_t min_value, i
     if (rc == ORACLE_NOMEM) return rc;
     if (below) return ORACLE_KEY_RANGE;
     return rc;
+}
+
+/* Bitmap sort of n 64-bit keys bounded by max_value: the same three steps
+ * as oracle_bitmap_sort over M = max_value + 1 values, with 64-bit keys and
+ * outputs (the bitmap has ceil(M / 32) words; max_value < 2^40 keeps it
+ * below 16 GiB, larger bounds are refused with -1). */
+int oracle_bitmap_sort_u64(const uint64_t *keys, uint64_t n, uint64_t max_value,
+                           uint64_t *out, uint64_t *count) {
+    if (max_value >= (1ull << 40)) return -1;
+    uint64_t M = max_value + 1u;
+    uint64_t words = (M + 31u) / 32u;
+    uint32_t *bitmap = (uint32_t *)calloc(words, sizeof(uint32_t));
+    if (bitmap == NULL) return ORACLE_NOMEM;
+    int out_of_range = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t x = keys[i];
+        if (x > max_value) { out_of_range = 1; continue; }
+        bitmap[x / 32u] = bitmap[x / 32u] | (1u << (x % 32u));
+    }
+    uint64_t k = 0;
+    for (uint64_t w = 0; w < words; ++w) {
+        if (bitmap[w] == 0) continue;
+        for (unsigned b = 0; b < 32u; ++b) {
+            if (bitmap[w] & (1u << b)) {
+                out[k] = w * 32u + b;
+                ++k;
+            }
+        }
+    }
+    free(bitmap);
+    *count = k;
+    if (out_of_range) return ORACLE_KEY_RANGE;
+    if (k < n) return ORACLE_DUPLICATE;
+    return ORACLE_OK;
 }

@@ -175,9 +175,36 @@ def check_paper_signed(o):
     assert st == KEY_RANGE and out.tolist() == [-3, 2, 7]
 
 
+def check_bitmap_u64(o):
+    # brute force over every subset of [0, M) for small M, in shuffled order
+    for M in range(1, 9):
+        for mask in range(1 << M):
+            keys = np.array([v for v in range(M) if mask >> v & 1], dtype=np.uint64)
+            keys = gen.shuffle(mask + 77, keys.astype(np.uint32)).astype(np.uint64)
+            st, out = o.bitmap_sort_u64(keys, M - 1)
+            assert st == OK and out.tolist() == _expected_from_mask(mask, M)
+    # values above 2^32: the library sort of distinct keys
+    base = gen.floyd(11, 20_000, 1 << 32).astype(np.uint64)
+    keys = (base << np.uint64(2)) | (base & np.uint64(3))          # distinct values below 2^34
+    st, out = o.bitmap_sort_u64(keys, (1 << 34) - 1)
+    assert st == OK and np.array_equal(out, np.sort(keys))
+    assert int(out[-1]) >= (1 << 32)
+    # a key above max_value is skipped and reported, also one that only
+    # differs above bit 31
+    st, out = o.bitmap_sort_u64(np.array([5, (1 << 32) + 5, 7], dtype=np.uint64), 100)
+    assert st == KEY_RANGE and out.tolist() == [5, 7]
+    st, out = o.bitmap_sort_u64(np.array([3, 3, 1], dtype=np.uint64), 3)
+    assert st == DUPLICATE and out.tolist() == [1, 3]
+    # below 2^32 it agrees with the 32-bit form
+    k32 = gen.floyd(12, 5_000, 1 << 20)
+    st32, o32 = o.bitmap_sort(k32, (1 << 20) - 1)
+    st64, o64 = o.bitmap_sort_u64(k32.astype(np.uint64), (1 << 20) - 1)
+    assert st32 == st64 == OK and np.array_equal(o32.astype(np.uint64), o64)
+
+
 ALL_CHECKS = [
     check_table1_or, check_bit_value_positions, check_table2_patterns,
     check_brute_force_subsets, check_all_permutations_small, check_closed_form_permutation,
     check_against_library_sort, check_invariants, check_edge_cases, check_duplicates,
-    check_paper_algorithm, check_theorem1_invariant, check_paper_signed,
+    check_paper_algorithm, check_theorem1_invariant, check_paper_signed, check_bitmap_u64,
 ]
