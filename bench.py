@@ -311,7 +311,11 @@ def run_plain(args, w, ws, rank, local):
     assert int(hres[0]) & 0xFFFFFFFF == bs.OK and int(hres[1]) == n
     assert bool(np.all(np.diff(hout.numpy().view(np.uint32)[:1 << 20].astype(np.int64)) > 0))
 
-    cub = time_cub(keys, M, flush, stream, args.steps) if not args.no_cub else None
+    comparison = None
+    if not args.no_cub:
+        comparison = {"cub": time_cub(keys, M, flush, stream, args.steps),
+                      "multiset": time_multiset(ctx, keys, M, flush, stream, args.steps, 0, peak),
+                      "multiset_1bit": time_multiset(ctx, keys, M, flush, stream, 3, 1, peak)}
 
     if rank != 0:
         return
@@ -340,7 +344,7 @@ def run_plain(args, w, ws, rank, local):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
-        "comparison": cub,
+        "comparison": comparison,
     }
     print(json.dumps(line), flush=True)
 
@@ -363,6 +367,50 @@ class L2Flush:
         self.w.fill_(v)
         if self.r is not None:
             self.sink += self.r.sum()
+
+
+def time_multiset(ctx, keys, M, flush, stream, steps, split_bits, peak):
+    """The multiset path (Algorithm 1's stable bit splits, split_bits bits
+    per pass; 0 = fewest passes of at most 8 bits) on the same keys: whole
+    call time, and the split kernels' bandwidth (8 bytes per key per pass)."""
+    import torch
+    n = keys.numel()
+    out = torch.empty_like(keys)
+    res = torch.zeros(2, dtype=torch.int64, device="cuda")
+    bits = max(1, (M - 1).bit_length())
+    if split_bits:
+        d, p = split_bits, -(-bits // split_bits)
+    else:
+        p = -(-bits // 8)
+        d = -(-bits // p)
+    ctx.multiset_async(keys, M - 1, split_bits, out=out, result=res, stream=stream)
+    torch.cuda.synchronize()
+    ok = int(res[0]) & 0xFFFFFFFF == 0 and int(res[1]) == n   # status OK
+    ok = ok and bool(torch.all(out[1:].to(torch.int64) & 0xFFFFFFFF >= out[:-1].to(torch.int64) & 0xFFFFFFFF))
+    reps = max(3, min(steps, 100))
+    ms = []
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.multiset_async(keys, M - 1, split_bits, out=out, result=res, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = float(np.median(ms))
+    ctx.set_phase_timing(True)
+    split = []
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        ctx.multiset_async(keys, M - 1, split_bits, out=out, result=res, stream=stream)
+        torch.cuda.synchronize()
+        split.append(dict(ctx.phase_times()).get("msplit", 0.0))
+    ctx.set_phase_timing(False)
+    per_pass = float(np.median(split)) / p
+    gbs = 8 * n / (per_pass * 1e-3) / 1e9 if per_pass > 0 else None
+    return {"impl": "bitsort_multiset (Algorithm 1, stable splits)", "split_bits": d, "passes": p, "ms": t,
+            "gkeys_s": n / (t * 1e-3) / 1e9, "sorted": ok, "split_ms_per_pass": per_pass,
+            "split_gbs": gbs, "split_frac": gbs / peak if gbs else None}
 
 
 def time_cub(keys, M, flush, stream, steps):

@@ -126,6 +126,37 @@ bitsort_status_t bitsort_ex(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n
 bitsort_status_t bitsort_i32(bitsort_ctx_t *ctx, const int32_t *keys, uint64_t n, int32_t min_value,
                              int32_t max_value, int32_t *out, bitsort_result_t *d_result, bitsort_stream_t stream);
 
+/* Sort n uint32 keys that MAY REPEAT, bounded by max_value: the paper's
+ * Algorithm 1 itself (Section V, first function): stable splits of the keys
+ * by their bits, least significant first, split_bits bits per pass (1..8;
+ * 1 = the paper's one bit per pass; 0 = the fewest passes of at most 8 bits
+ * that cover the bits of max_value).  Every key is written once per pass;
+ * the result is the ascending order of the multiset (Theorem 1).
+ *   - keys, out: DEVICE pointers to n uint32; keys == out sorts in place
+ *     (through the context's buffer); other overlaps -> BITSORT_ERR_INVALID.
+ *   - n >= 2^32, split_bits > 8 or misaligned pointers -> BITSORT_ERR_INVALID,
+ *     nothing enqueued.
+ *   - A key above max_value -> BITSORT_ERR_KEY_RANGE (out then holds the keys
+ *     ordered by the bits below the range's width only); count is always n.
+ *     Reported through d_result (DEVICE, nullable = the context) like
+ *     bitsort_ex().
+ *   - Scratch (grown on demand, owned by the context): a buffer of n keys
+ *     (shared with the bitmap path), ceil(n / 4096) x 2^split_bits look-back
+ *     words and a 4.4 KB block.  Calls on one context are stream-ordered on
+ *     the stream they are given: do not run two at once on one context. */
+bitsort_status_t bitsort_multiset(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n, uint32_t max_value,
+                                  uint32_t split_bits, uint32_t *out, bitsort_result_t *d_result,
+                                  bitsort_stream_t stream);
+
+/* As bitsort_multiset() for SIGNED int32 keys in [min_value, max_value]
+ * (Algorithm 1's second function sorts the negative and the nonnegative keys
+ * apart and joins them; the same order comes from splitting the offsets
+ * x - min_value modulo 2^32).  min_value > max_value -> BITSORT_ERR_INVALID;
+ * a key outside the range -> BITSORT_ERR_KEY_RANGE. */
+bitsort_status_t bitsort_multiset_i32(bitsort_ctx_t *ctx, const int32_t *keys, uint64_t n, int32_t min_value,
+                                      int32_t max_value, uint32_t split_bits, int32_t *out,
+                                      bitsort_result_t *d_result, bitsort_stream_t stream);
+
 /* Wait for `stream`, then return the status of the last sort that wrote its
  * outcome into the context (and its count through `count`, nullable). */
 bitsort_status_t bitsort_sync_status(bitsort_ctx_t *ctx, bitsort_stream_t stream, uint64_t *count);

@@ -31,7 +31,7 @@ PATH_NAMES = {0: "auto", 1: "fused", 2: "partition", 3: "global"}
 # names every build must export (checked by the CPU test-suite)
 EXPORTS = [
     "bitsort_ctx_create", "bitsort_ctx_destroy", "bitsort_status_string", "bitsort_last_error", "bitsort",
-    "bitsort_ex", "bitsort_i32",
+    "bitsort_ex", "bitsort_i32", "bitsort_multiset", "bitsort_multiset_i32",
     "bitsort_sync_status", "bitsort_batched", "bitsort_batch_plan_create", "bitsort_batch_plan_launch",
     "bitsort_batch_plan_results", "bitsort_batch_plan_device_results", "bitsort_batch_plan_destroy",
     "bitsort_server_create", "bitsort_server_submit", "bitsort_server_wait", "bitsort_server_stats",
@@ -97,6 +97,8 @@ def _declare(lib):
         "bitsort": (st, [p, ctypes.c_size_t, u32, p, p]),
         "bitsort_ex": (st, [p, p, u64, u32, p, p, p]),
         "bitsort_i32": (st, [p, p, u64, ctypes.c_int32, ctypes.c_int32, p, p, p]),
+        "bitsort_multiset": (st, [p, p, u64, u32, u32, p, p, p]),
+        "bitsort_multiset_i32": (st, [p, p, u64, ctypes.c_int32, ctypes.c_int32, u32, p, p, p]),
         "bitsort_sync_status": (st, [p, p, ctypes.POINTER(u64)]),
         "bitsort_batched": (st, [p, p, ctypes.c_size_t, p, p]),
         "bitsort_batch_plan_create": (st, [p, p, ctypes.c_size_t, ctypes.POINTER(p)]),
@@ -227,6 +229,41 @@ class Context:
         st, cnt = self.sync_status(stream)
         return st, cnt, out
 
+    def multiset_async(self, keys, max_value: int, split_bits: int = 0, out=None, result=None, stream=None):
+        """Enqueue Algorithm 1 (stable bit splits; keys may repeat) on `keys`; returns out."""
+        import torch
+        if out is None:
+            out = torch.empty_like(keys)
+        rptr = result.data_ptr() if result is not None else None
+        st = load().bitsort_multiset(self.handle, _ptr(keys) if keys.numel() else None, keys.numel(),
+                                     int(max_value), int(split_bits), _ptr(out) if out.numel() else None, rptr,
+                                     _stream_handle(stream))
+        _check(st, "bitsort_multiset")
+        return out
+
+    def multiset(self, keys, max_value: int, split_bits: int = 0, out=None, stream=None):
+        """Multiset sort and wait: returns (status, count, out)."""
+        out = self.multiset_async(keys, max_value, split_bits, out=out, stream=stream)
+        st, cnt = self.sync_status(stream)
+        return st, cnt, out
+
+    def multiset_i32_async(self, keys, min_value: int, max_value: int, split_bits: int = 0, out=None,
+                           result=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(keys)
+        rptr = result.data_ptr() if result is not None else None
+        st = load().bitsort_multiset_i32(self.handle, _ptr(keys) if keys.numel() else None, keys.numel(),
+                                         int(min_value), int(max_value), int(split_bits),
+                                         _ptr(out) if out.numel() else None, rptr, _stream_handle(stream))
+        _check(st, "bitsort_multiset_i32")
+        return out
+
+    def multiset_i32(self, keys, min_value: int, max_value: int, split_bits: int = 0, out=None, stream=None):
+        out = self.multiset_i32_async(keys, min_value, max_value, split_bits, out=out, stream=stream)
+        st, cnt = self.sync_status(stream)
+        return st, cnt, out
+
     def sync_status(self, stream=None):
         cnt = ctypes.c_uint64(0)
         st = load().bitsort_sync_status(self.handle, _stream_handle(stream), ctypes.byref(cnt))
@@ -282,7 +319,8 @@ class Context:
         kinds = (ctypes.c_int * 8)()
         cnt = ctypes.c_int(0)
         _check(load().bitsort_phase_times(self.handle, ms, kinds, ctypes.byref(cnt)), "bitsort_phase_times")
-        names = {-1: "persistent", 0: "hist", 1: "part", 2: "bucket", 3: "gscatter", 4: "gscan", 5: "parts"}
+        names = {-1: "persistent", 0: "hist", 1: "part", 2: "bucket", 3: "gscatter", 4: "gscan", 5: "parts",
+                 6: "mhist", 7: "msplit"}
         return [(names.get(kinds[i], kinds[i]), ms[i]) for i in range(cnt.value)]
 
     def kernel_launches(self) -> int:

@@ -127,6 +127,7 @@ extern "C" bitsort_status_t bitsort_ctx_destroy(bitsort_ctx_t *c) {
     if (c->part) cudaFree(c->part);
     if (c->bitmap) cudaFree(c->bitmap);
     if (c->flush) cudaFree(c->flush);
+    bsx_multiset_free(c);
     for (int i = 0; i < 9; ++i)
         if (c->tev[i]) cudaEventDestroy(c->tev[i]);
     delete c;
@@ -287,7 +288,7 @@ bool bsx_ranges_overlap(const void *a, const void *b, uint64_t bytes) {
     return x < y + bytes && y < x + bytes;
 }
 
-static bitsort_status_t ensure_part(bitsort_ctx *c, uint64_t n) {
+bitsort_status_t bsx_ensure_part(bitsort_ctx *c, uint64_t n) {
     if (c->part_cap >= n) return BITSORT_OK;
     if (c->part) {
         cudaDeviceSynchronize();
@@ -380,12 +381,12 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     a.bias = bias;
     bool alias = keys == out;
     if (cfg.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
-        bitsort_status_t st = ensure_part(c, (uint64_t)a.nslices * a.cap);
+        bitsort_status_t st = bsx_ensure_part(c, (uint64_t)a.nslices * a.cap);
         if (st != BITSORT_OK) return st;
         a.part = c->part;
     } else if (cfg.path == BITSORT_PATH_PARTITION) {
         if (alias) {
-            bitsort_status_t st = ensure_part(c, n);
+            bitsort_status_t st = bsx_ensure_part(c, n);
             if (st != BITSORT_OK) return st;
             a.part = c->part;
         } else {

@@ -53,6 +53,13 @@ struct bitsort_ctx {
     void *flush = nullptr;        // L2 flush buffer for tuning
     size_t flush_bytes = 0;
 
+    // multiset path (msort.cu): look-back words tagged with a pass epoch
+    // (never cleared between passes) and a small block cleared per call
+    uint64_t *ms_look = nullptr;
+    uint64_t ms_look_words = 0;
+    uint32_t ms_epoch = 0;        // epoch of the last pass launched
+    uint32_t *ms_misc = nullptr;
+
     // optional per-phase timing of single sorts
     bool timing = false;
     cudaEvent_t tev[9] = {};
@@ -94,6 +101,8 @@ bool bsx_ranges_overlap(const void *a, const void *b, uint64_t bytes);
 int bsx_grid_for(bitsort_ctx *c, int threads, uint32_t smem, uint32_t items);
 bitsort_status_t bsx_validate(const uint32_t *keys, uint64_t n, uint32_t max_value, const uint32_t *out);
 bitsort_status_t bsx_reset_scratch(bitsort_ctx *c);
+bitsort_status_t bsx_ensure_part(bitsort_ctx *c, uint64_t n);
+void bsx_multiset_free(bitsort_ctx *c);
 
 // batch plans (batch.cu)
 bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, size_t count,

@@ -57,3 +57,20 @@ def test_dense_full_range_2e31_properties(ctx):
     del out
     inv = gen.feistel_inverse(gen.SEED_BASE + 2, M, host)
     assert int(inv.max()) < n
+
+
+@pytest.mark.parametrize("n,M,kind", [
+    (1 << 24, 1 << 28, "distinct"),    # the benchmark's keys
+    (1 << 24, 1 << 20, "repeat"),      # 16 keys per value on average
+    (1 << 24, 1 << 32, "repeat"),      # full 32-bit values, four passes of 8 bits
+])
+def test_multiset_full_size(ctx, n, M, kind):
+    """The multiset path (Algorithm 1's stable bit splits) at the benchmark's
+    size, compared with the CPU oracle's Algorithm 1 element by element."""
+    if kind == "distinct":
+        keys_np = gen.keys(gen.SEED_BASE + 1, n, M, "floyd")
+    else:
+        keys_np = gen.uniform_with_replacement(gen.SEED_BASE + 90, n, M)
+    st, cnt, out = ctx.multiset(to_dev(keys_np), M - 1)
+    assert st == bs.OK and cnt == n
+    assert np.array_equal(to_host(out), oracle.paper_sort_u32(keys_np))
