@@ -126,6 +126,26 @@ bitsort_status_t bitsort_ex(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n
 bitsort_status_t bitsort_i32(bitsort_ctx_t *ctx, const int32_t *keys, uint64_t n, int32_t min_value,
                              int32_t max_value, int32_t *out, bitsort_result_t *d_result, bitsort_stream_t stream);
 
+/* The bitmap sort for keys stored in 16, 8 and 64 bits (Algorithm 1 is
+ * written for any integer type T; Section V).  Same contract as bitsort_ex()
+ * (distinct keys bounded by max_value, keys == out allowed, other overlaps,
+ * null pointers, misalignment for the type or n > max_value + 1 ->
+ * BITSORT_ERR_INVALID; KEY_RANGE / DUPLICATE through d_result or the
+ * context, count = values written).
+ *   - bitsort_u16 / bitsort_u8: the whole value range (at most 65,536 values)
+ *     is one shared-memory bitmap: one kernel, one CTA.
+ *   - bitsort_u64: max_value must be below 2^32 (else BITSORT_ERR_INVALID);
+ *     keys are narrowed to 32 bits into a context-owned copy (n x 4 bytes,
+ *     grown on demand), sorted by the 32-bit path and widened into out.  A
+ *     key above max_value, also one differing only above bit 31, is skipped
+ *     and reported as KEY_RANGE. */
+bitsort_status_t bitsort_u16(bitsort_ctx_t *ctx, const uint16_t *keys, uint64_t n, uint16_t max_value,
+                             uint16_t *out, bitsort_result_t *d_result, bitsort_stream_t stream);
+bitsort_status_t bitsort_u8(bitsort_ctx_t *ctx, const uint8_t *keys, uint64_t n, uint8_t max_value, uint8_t *out,
+                            bitsort_result_t *d_result, bitsort_stream_t stream);
+bitsort_status_t bitsort_u64(bitsort_ctx_t *ctx, const uint64_t *keys, uint64_t n, uint64_t max_value,
+                             uint64_t *out, bitsort_result_t *d_result, bitsort_stream_t stream);
+
 /* Sort n uint32 keys that MAY REPEAT, bounded by max_value: the paper's
  * Algorithm 1 itself (Section V, first function): stable splits of the keys
  * by their bits, least significant first, split_bits bits per pass (1..8;

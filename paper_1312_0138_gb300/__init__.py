@@ -31,7 +31,8 @@ PATH_NAMES = {0: "auto", 1: "fused", 2: "partition", 3: "global"}
 # names every build must export (checked by the CPU test-suite)
 EXPORTS = [
     "bitsort_ctx_create", "bitsort_ctx_destroy", "bitsort_status_string", "bitsort_last_error", "bitsort",
-    "bitsort_ex", "bitsort_i32", "bitsort_multiset", "bitsort_multiset_i32",
+    "bitsort_ex", "bitsort_i32", "bitsort_multiset", "bitsort_multiset_i32", "bitsort_u16", "bitsort_u8",
+    "bitsort_u64",
     "bitsort_sync_status", "bitsort_batched", "bitsort_batch_plan_create", "bitsort_batch_plan_launch",
     "bitsort_batch_plan_results", "bitsort_batch_plan_device_results", "bitsort_batch_plan_destroy",
     "bitsort_server_create", "bitsort_server_submit", "bitsort_server_wait", "bitsort_server_stats",
@@ -98,6 +99,9 @@ def _declare(lib):
         "bitsort_ex": (st, [p, p, u64, u32, p, p, p]),
         "bitsort_i32": (st, [p, p, u64, ctypes.c_int32, ctypes.c_int32, p, p, p]),
         "bitsort_multiset": (st, [p, p, u64, u32, u32, p, p, p]),
+        "bitsort_u16": (st, [p, p, u64, ctypes.c_uint16, p, p, p]),
+        "bitsort_u8": (st, [p, p, u64, ctypes.c_uint8, p, p, p]),
+        "bitsort_u64": (st, [p, p, u64, u64, p, p, p]),
         "bitsort_multiset_i32": (st, [p, p, u64, ctypes.c_int32, ctypes.c_int32, u32, p, p, p]),
         "bitsort_sync_status": (st, [p, p, ctypes.POINTER(u64)]),
         "bitsort_batched": (st, [p, p, ctypes.c_size_t, p, p]),
@@ -164,14 +168,14 @@ def _stream_handle(stream) -> int:
     return stream.cuda_stream
 
 
-def _ptr(t) -> int:
+def _ptr(t, dtypes=None) -> int:
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError("expected a torch tensor")
     if not t.is_cuda:
         raise ValueError("tensor must be on a CUDA device")
-    if t.dtype not in (torch.int32, torch.uint32):
-        raise TypeError("keys/out must be int32 or uint32 tensors (uint32 values)")
+    if t.dtype not in (dtypes or (torch.int32, torch.uint32)):
+        raise TypeError(f"keys/out of type {t.dtype}: expected one of {dtypes or (torch.int32, torch.uint32)}")
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return t.data_ptr()
@@ -226,6 +230,29 @@ class Context:
     def sort_i32(self, keys, min_value: int, max_value: int, out=None, stream=None):
         """Signed sort and wait: returns (status, count, out)."""
         out = self.sort_i32_async(keys, min_value, max_value, out=out, stream=stream)
+        st, cnt = self.sync_status(stream)
+        return st, cnt, out
+
+    def sort_width_async(self, keys, max_value: int, out=None, result=None, stream=None):
+        """Bitmap sort of 16-, 8- or 64-bit keys (torch int16 / uint8 / int64
+        tensors holding the unsigned values); returns out."""
+        import torch
+        fn = {torch.int16: "bitsort_u16", torch.uint8: "bitsort_u8", torch.int64: "bitsort_u64"}.get(keys.dtype)
+        if fn is None:
+            raise TypeError(f"no bitmap sort for keys of type {keys.dtype}")
+        if out is None:
+            out = torch.empty_like(keys)
+        rptr = result.data_ptr() if result is not None else None
+        dt = (keys.dtype,)
+        st = getattr(load(), fn)(self.handle, _ptr(keys, dt) if keys.numel() else None, keys.numel(),
+                                 int(max_value), _ptr(out, dt) if out.numel() else None, rptr,
+                                 _stream_handle(stream))
+        _check(st, fn)
+        return out
+
+    def sort_width(self, keys, max_value: int, out=None, stream=None):
+        """Width sort and wait: returns (status, count, out)."""
+        out = self.sort_width_async(keys, max_value, out=out, stream=stream)
         st, cnt = self.sync_status(stream)
         return st, cnt, out
 

@@ -128,6 +128,7 @@ extern "C" bitsort_status_t bitsort_ctx_destroy(bitsort_ctx_t *c) {
     if (c->bitmap) cudaFree(c->bitmap);
     if (c->flush) cudaFree(c->flush);
     bsx_multiset_free(c);
+    bsx_widths_free(c);
     for (int i = 0; i < 9; ++i)
         if (c->tev[i]) cudaEventDestroy(c->tev[i]);
     delete c;

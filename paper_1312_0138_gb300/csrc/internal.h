@@ -60,6 +60,11 @@ struct bitsort_ctx {
     uint32_t ms_epoch = 0;        // epoch of the last pass launched
     uint32_t *ms_misc = nullptr;
 
+    // 64-bit keys (widths.cu): the narrowed 32-bit copy and a flag block
+    uint32_t *wide = nullptr;
+    uint64_t wide_cap = 0;
+    void *wide_misc = nullptr;
+
     // optional per-phase timing of single sorts
     bool timing = false;
     cudaEvent_t tev[9] = {};
@@ -103,6 +108,7 @@ bitsort_status_t bsx_validate(const uint32_t *keys, uint64_t n, uint32_t max_val
 bitsort_status_t bsx_reset_scratch(bitsort_ctx *c);
 bitsort_status_t bsx_ensure_part(bitsort_ctx *c, uint64_t n);
 void bsx_multiset_free(bitsort_ctx *c);
+void bsx_widths_free(bitsort_ctx *c);
 
 // batch plans (batch.cu)
 bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, size_t count,
