@@ -141,15 +141,20 @@ __device__ uint32_t tile_lookback(const uint64_t *look, uint32_t tile, uint32_t 
             if (flag == 2) return excl;
         }
         top -= w;
-        if (w == 0) {   // the nearest one is not published yet
-            if (spins == 0) t0 = now_ns();
-            ++spins;
-            if (spins > cap ||
-                ((spins & 15) == 0 && (now_ns() - t0 > limit_ns || ld_acquire_u32(timeout) != 0))) {
-                atomicOr(timeout, 1u);
-                return excl;
+        if (w < kWindow && top >= 0) {   // wait for that one alone before reading a window again
+            const uint64_t *p = look + (uint64_t)top * R + g;
+            while (true) {
+                const uint64_t u = ld_relaxed_u64(p);
+                if ((uint32_t)(u >> kEpochShift) == epoch && ((uint32_t)(u >> 32) & 3u) != 0) break;
+                if (spins == 0) t0 = now_ns();
+                ++spins;
+                if (spins > cap ||
+                    ((spins & 15) == 0 && (now_ns() - t0 > limit_ns || ld_acquire_u32(timeout) != 0))) {
+                    atomicOr(timeout, 1u);
+                    return excl;
+                }
+                __nanosleep(32);
             }
-            __nanosleep(32);
         }
     }
     return excl;
@@ -246,6 +251,7 @@ __global__ void __launch_bounds__(kT, 4) ms_pass_kernel(PassArgs a) {
             peers &= bit ? bb : ~bb;
         }
         // valid lanes: `peers` = the valid lanes of this step in the same group
+        // (one ballot per group bit: cheaper here than a warp match)
         const uint32_t below = __popc(peers & lt);
         uint32_t old = 0;
         if (valid && below == 0) {   // the group's first lane adds the step's keys of the group
