@@ -374,6 +374,10 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
                                       uint64_t M, uint32_t *out, bitsort_result_t *d_result, cudaStream_t stream,
                                       uint32_t stall, uint32_t bias = 0) {
     bsx_config cfg = fit_smem(c, bsx_sanitize(cfg0, n, M), n, M);
+    // in place, a capacity bucket that overflowed (repeated keys) would read
+    // the whole input while other slices write their outputs over it: exact
+    // bucket ranges never overflow
+    if (keys == out && cfg.path == BITSORT_PATH_PARTITION && cfg.layout == LAYOUT_CAPACITY) cfg.layout = LAYOUT_EXACT;
     EngineParams p;
     memset(&p, 0, sizeof(p));
     ArrayDesc &a = p.one;

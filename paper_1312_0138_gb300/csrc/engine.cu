@@ -75,6 +75,8 @@ struct SharedMisc {
     uint32_t total;
     uint32_t summ_clean;   // the summary bitmap (start of shared memory) is all zero
     uint32_t bm_clean_w;   // the slice bitmap's first bm_clean_w words are zero
+    uint64_t known;        // PARTITION: output offset of the slice's bucket (thread 0)
+    uint64_t expect;       // PARTITION: keys the bucket received (thread 0)
 };
 
 // Thread 0 only: wait until *p >= target.  Gives up (false) when the array's
@@ -513,6 +515,32 @@ __device__ __forceinline__ uint32_t count_words(const uint32_t *bm, uint32_t w0,
 // number of set bits of all earlier slices by look-back, and leave in shared
 // memory: m.excl (first output index of the slice), m.total (its set bits),
 // m.wbase[w] (set bits before warp w's range).  Returns the warp's range.
+// The partition path knows where each bucket's outputs start: with distinct
+// keys, a bucket's set bits equal its key count, so the slice starts at the
+// bucket's histogram offset (EXACT layout) or at the sum of the fill counts
+// of the buckets before it (CAPACITY layout), computed by the slice's
+// thread 0 into m.known / m.expect.  The slice records (start, count) in its
+// look-back word for the array's last CTA; one whose count falls short of
+// its bucket's keys (repeated keys) raises the mismatch flag, and the last
+// CTA then closes the gaps (slice_complete).  Without a partition (GLOBAL
+// path) the slices chain through the decoupled look-back.
+__device__ __forceinline__ bool known_offsets(const ArrayDesc &a) {
+    return a.path == BITSORT_PATH_PARTITION && a.nslices > 1;
+}
+
+// Called by warp 0 of the CTA that owns slice s (lane 0 reads m.known).
+__device__ uint64_t slice_offset(const EngineParams &P, const ArrayDesc &a, uint32_t s, uint32_t total, int lane,
+                                 const SharedMisc &m) {
+    if (known_offsets(a)) {
+        if (lane == 0) {
+            a.look[s] = (m.known << 32) | total;
+            if (total != m.expect) atomicOr(&a.sync[SY_MISMATCH], 1u);
+        }
+        return m.known;
+    }
+    return a.nslices > 1 ? lookback(P, a, s, total, lane) : 0;
+}
+
 template <int T>
 __device__ void slice_count(const EngineParams &P, const ArrayDesc &a, uint32_t s, const uint32_t *bm,
                             uint32_t words, uint32_t wpl, uint32_t &w0, uint32_t &w1, SharedMisc &m,
@@ -534,7 +562,7 @@ __device__ void slice_count(const EngineParams &P, const ArrayDesc &a, uint32_t 
         if (lane < NW) m.wbase[lane] = incl - c;
         const uint32_t total = __shfl_sync(kFull, incl, 31);
         uint64_t excl = 0;
-        if (with_lookback && a.nslices > 1) excl = lookback(P, a, s, total, lane);
+        if (with_lookback) excl = slice_offset(P, a, s, total, lane, m);
         if (lane == 0) {
             m.excl = excl;
             m.total = total;
@@ -547,14 +575,18 @@ __device__ void slice_count(const EngineParams &P, const ArrayDesc &a, uint32_t 
 template <int T>
 __device__ void slice_lookback(const EngineParams &P, const ArrayDesc &a, uint32_t s, SharedMisc &m) {
     if (threadIdx.x < 32) {
-        const uint64_t excl = a.nslices > 1 ? lookback(P, a, s, m.total, threadIdx.x) : 0;
+        const uint64_t excl = slice_offset(P, a, s, m.total, threadIdx.x, m);
         if (threadIdx.x == 0) m.excl = excl;
     }
     __syncthreads();
 }
 
 // The CTA that finishes the array's last slice writes the outcome and
-// returns the array's scratch to its zero state for the next launch.
+// returns the array's scratch to its zero state for the next launch.  On the
+// partition path it also sums the slices' counts and, if some slice held
+// fewer set bits than its bucket had keys (repeated keys), moves every
+// slice's outputs down, in slice order, to close the gaps: each chunk of T
+// values is read whole before it is written, and a slice never moves up.
 template <int T>
 __device__ void slice_complete(const ArrayDesc &a, SharedMisc &m) {
     // the barrier orders the block's writes before thread 0's fence, which
@@ -568,21 +600,55 @@ __device__ void slice_complete(const ArrayDesc &a, SharedMisc &m) {
         if (m.flag) __threadfence();
     }
     __syncthreads();
-    if (m.flag) {
-        uint64_t total = m.total;
+    if (!m.flag) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t total = m.total;
+    if (known_offsets(a)) {
+        uint64_t part = 0;
+        for (uint32_t i = threadIdx.x; i < a.nslices; i += T) part += (uint32_t)__ldcg(&a.look[i]);
+        part = warp_sum_u64(part);
+        if (lane == 0) m.wsum[warp] = part;
+        __syncthreads();
+        total = 0;
+        for (int w = 0; w < T / 32; ++w) total += m.wsum[w];
+        const bool gaps = ld_acquire_u32(&a.sync[SY_MISMATCH]) != 0 && ld_acquire_u32(&a.sync[SY_TIMEOUT]) == 0;
+        if (gaps) {
+            uint32_t *out = a.out;
+            uint64_t dst = 0;
+            for (uint32_t i = 0; i < a.nslices; ++i) {
+                const uint64_t v = __ldcg(&a.look[i]);
+                const uint64_t src = v >> 32, cnt = (uint32_t)v;
+                if (src != dst) {
+                    for (uint64_t k = 0; k < cnt; k += T) {
+                        const uint64_t j = k + threadIdx.x;
+                        const uint32_t x = j < cnt ? __ldcg(out + src + j) : 0u;
+                        __syncthreads();
+                        if (j < cnt) out[dst + j] = x;
+                        __syncthreads();
+                    }
+                }
+                dst += cnt;
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < a.nslices; i += T) {
+            a.look[i] = 0;
+            a.cursor[i] = 0;
+        }
+    } else {
         if (a.nslices > 1) total = ld_acquire_u64(&a.look[a.nslices - 1]) & LB_VALUE;
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < a.nslices && a.nslices > 1; i += T) a.look[i] = 0;
-        if (threadIdx.x == 0) {
-            uint32_t st = BITSORT_OK;
-            if (ld_acquire_u32(&a.sync[SY_TIMEOUT]) != 0) st = BITSORT_ERR_TIMEOUT;
-            else if (ld_acquire_u32(&a.sync[SY_RANGE]) != 0) st = BITSORT_ERR_KEY_RANGE;
-            else if (total < a.n) st = BITSORT_ERR_DUPLICATE;
-            a.result->status = st;
-            a.result->reserved = 0;
-            a.result->count = total;
-            for (int k = 0; k < SY_COUNT; ++k) a.sync[k] = 0;
-        }
+    }
+    if (threadIdx.x == 0) {
+        uint32_t st = BITSORT_OK;
+        if (ld_acquire_u32(&a.sync[SY_TIMEOUT]) != 0) st = BITSORT_ERR_TIMEOUT;
+        else if (ld_acquire_u32(&a.sync[SY_RANGE]) != 0) st = BITSORT_ERR_KEY_RANGE;
+        else if (total < a.n) st = BITSORT_ERR_DUPLICATE;
+        a.result->status = st;
+        a.result->reserved = 0;
+        a.result->count = total;
+        for (int k = 0; k < SY_COUNT; ++k) a.sync[k] = 0;
     }
 }
 
@@ -982,7 +1048,7 @@ __device__ void slice_finish_sparse(const EngineParams &P, const ArrayDesc &a, u
         const uint32_t incl = warp_incl_scan_u32(c, lane);
         if (lane < NW) m.wbase[lane] = incl - c;
         const uint32_t total = __shfl_sync(kFull, incl, 31);
-        const uint64_t excl = a.nslices > 1 ? lookback(P, a, s, total, lane) : 0;
+        const uint64_t excl = slice_offset(P, a, s, total, lane, m);
         if (lane == 0) {
             m.excl = excl;
             m.total = total;
@@ -1054,10 +1120,21 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
             lo = (uint64_t)b * a.cap;
             hi = lo + filled;
         }
+        if (known_offsets(a)) {   // the slice starts after the keys of the buckets before it
+            uint64_t before = 0;
+            for (uint32_t i = threadIdx.x; i < b; i += T) before += __ldcg(&a.cursor[i]);
+            before = warp_sum_u64(before);
+            if ((threadIdx.x & 31) == 0) m.wsum[threadIdx.x >> 5] = before;
+            if (threadIdx.x == 0) m.expect = filled;
+        }
     } else if (partitioned) {
         src = a.part;
         lo = min(__ldcg(&a.offsets[b]), a.n);
         hi = lo + min((uint64_t)__ldcg(&a.counts[b]), a.n - lo);
+        if (threadIdx.x == 0) {
+            m.known = lo;
+            m.expect = hi - lo;
+        }
     }
     if (!m.flag) hi = lo;
     // sparse slice: at most one key per four bitmap words (summary bitmap)
@@ -1070,7 +1147,14 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
         for (uint32_t i = threadIdx.x; i < w4 / 4; i += T) bm4[i] = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
-    if (threadIdx.x == 0) m.summ_clean = 1u;
+    if (threadIdx.x == 0) {
+        m.summ_clean = 1u;
+        if (partitioned && a.layout == LAYOUT_CAPACITY && known_offsets(a)) {
+            uint64_t before = 0;
+            for (int w = 0; w < NW; ++w) before += m.wsum[w];
+            m.known = before;
+        }
+    }
 
     const uint32_t bias = a.bias;
     const uint32_t base = (uint32_t)v0 + bias, span = (uint32_t)vals;   // slice values: x - base in [0, span)
@@ -1112,7 +1196,7 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
     if (partitioned && threadIdx.x == 0) {
         a.counts[b] = 0;
-        a.cursor[b] = 0;
+        if (a.nslices == 1) a.cursor[b] = 0;   // else the last CTA clears the cursors (known offsets)
     }
     if (sparse) {
         slice_finish_sparse<T>(P, a, b, bm, summ, words, base, m);

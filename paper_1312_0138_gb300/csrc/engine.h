@@ -40,6 +40,7 @@ enum SyncSlot : uint32_t {
     SY_TIMEOUT = 4,       // a bounded wait ran out
     SY_SLICES_DONE = 5,   // BUCKET / GSCAN items finished
     SY_OVERFLOW = 6,      // CAPACITY layout: a bucket got more keys than it can hold
+    SY_MISMATCH = 7,      // PARTITION: a slice holds fewer set bits than its bucket had keys
     SY_COUNT = 8
 };
 

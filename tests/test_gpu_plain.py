@@ -155,6 +155,23 @@ def test_capacity_overflow_from_repeated_keys(ctx, persistent):
     rest = gen.floyd(21, 20_000, 1 << 18)
     keys = gen.shuffle(22, np.concatenate([rep, rest]))
     check(ctx, keys, (1 << 18) - 1, path=bs.PATH_PARTITION, S=4096, layout=1, persistent=persistent)
+    check(ctx, keys, (1 << 18) - 1, path=bs.PATH_PARTITION, S=4096, layout=1, persistent=persistent, inplace=True)
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_repeats_spread_over_many_slices(ctx, layout, persistent):
+    # repeated keys in many buckets: every slice after the first short one
+    # is moved down to close the gaps; also in place
+    keys = gen.uniform_with_replacement(31, 200_000, 1 << 20)
+    for S in (4096, 1 << 16):
+        check(ctx, keys, (1 << 20) - 1, path=bs.PATH_PARTITION, S=S, layout=layout, persistent=persistent)
+        check(ctx, keys, (1 << 20) - 1, path=bs.PATH_PARTITION, S=S, layout=layout, persistent=persistent,
+              inplace=True)
+    # a single repeat near the end: only the last slices move
+    keys = gen.floyd(32, 150_000, 1 << 20)
+    keys[-1] = keys[0]
+    check(ctx, keys, (1 << 20) - 1, path=bs.PATH_PARTITION, S=4096, layout=layout, persistent=persistent)
 
 
 @pytest.mark.parametrize("name,strat", STRATS, ids=[x[0] for x in STRATS])
