@@ -77,6 +77,8 @@ struct SharedMisc {
     uint32_t bm_clean_w;   // the slice bitmap's first bm_clean_w words are zero
     uint64_t known;        // PARTITION: output offset of the slice's bucket (thread 0)
     uint64_t expect;       // PARTITION: keys the bucket received (thread 0)
+    uint32_t defer;        // slices report their completion once per CTA, at the end of the kernel
+    uint32_t done_local;   // slices this CTA finished while deferring (thread 0)
 };
 
 // Thread 0 only: wait until *p >= target.  Gives up (false) when the array's
@@ -587,16 +589,19 @@ __device__ void slice_lookback(const EngineParams &P, const ArrayDesc &a, uint32
 // fewer set bits than its bucket had keys (repeated keys), moves every
 // slice's outputs down, in slice order, to close the gaps: each chunk of T
 // values is read whole before it is written, and a slice never moves up.
+// `count` slices are reported at once (a CTA that deferred its slices'
+// reports to the end of the kernel); a CTA with nothing to report must not
+// call it.
 template <int T>
-__device__ void slice_complete(const ArrayDesc &a, SharedMisc &m) {
+__device__ void complete_slices(const ArrayDesc &a, SharedMisc &m, uint32_t count) {
     // the barrier orders the block's writes before thread 0's fence, which
     // makes them visible device-wide before the completion count (and, for
     // the last CTA, the count before its reads)
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const uint32_t d = atomicAdd(&a.sync[SY_SLICES_DONE], 1u);
-        m.flag = (d == a.nslices - 1) ? 1u : 0u;
+        const uint32_t d = atomicAdd(&a.sync[SY_SLICES_DONE], count);
+        m.flag = (d + count == a.nslices) ? 1u : 0u;
         if (m.flag) __threadfence();
     }
     __syncthreads();
@@ -650,6 +655,18 @@ __device__ void slice_complete(const ArrayDesc &a, SharedMisc &m) {
         a.result->count = total;
         for (int k = 0; k < SY_COUNT; ++k) a.sync[k] = 0;
     }
+}
+
+// End of one slice: report it now, or count it for the CTA's report at the
+// end of the kernel (m.defer).
+template <int T>
+__device__ void slice_complete(const ArrayDesc &a, SharedMisc &m) {
+    if (m.defer) {
+        __syncthreads();
+        if (threadIdx.x == 0) ++m.done_local;
+        return;
+    }
+    complete_slices<T>(a, m, 1u);
 }
 
 // Count, look back and write out one bitmap slice held in shared memory by
@@ -1334,6 +1351,8 @@ __global__ void __launch_bounds__(T, 1024 / T) engine_kernel(const __grid_consta
     if (threadIdx.x == 0) {
         m.summ_clean = 0u;
         m.bm_clean_w = 0u;
+        m.defer = 0u;
+        m.done_local = 0u;
     }
     for (;;) {
         if (threadIdx.x == 0) m.ticket = atomicAdd(&P.ticket[0], 1u);
@@ -1394,10 +1413,26 @@ __global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constan
     if (threadIdx.x == 0) {
         m.summ_clean = 0u;
         m.bm_clean_w = 0u;
+        m.defer = 0u;
+        m.done_local = 0u;
     }
     pdl_wait();
     const ArrayDesc &a = P.one;
     if constexpr (TYPE == IT_BUCKET || TYPE == IT_GSCAN) {
+      if (TYPE == IT_BUCKET && (known_offsets(a) || a.nslices == 1)) {
+        // the slices do not wait on one another: a fixed share per CTA, one
+        // completion report per CTA
+        if (threadIdx.x == 0) m.defer = 1u;
+        __syncthreads();
+        for (uint32_t t = blockIdx.x; t < P.total_items; t += gridDim.x) {
+            item_bucket<T>(P, a, t, smem, m);
+            __syncthreads();
+        }
+        pdl_trigger();
+        const uint32_t done = m.done_local;
+        if (threadIdx.x == 0) m.defer = 0u;
+        if (done) complete_slices<T>(a, m, done);
+      } else {
         for (;;) {
             if (threadIdx.x == 0) m.ticket = atomicAdd(&P.ticket[0], 1u);
             __syncthreads();
@@ -1417,6 +1452,7 @@ __global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constan
                 __threadfence();
             }
         }
+      }
     } else if constexpr (TYPE == IT_PARTS) {
         part_stream<T>(P, a, smem, m);
         pdl_trigger();
