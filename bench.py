@@ -473,7 +473,8 @@ def run_batched(args, ws, rank, local):
     for _ in range(args.warmup):
         plan.launch()
     res = plan.results()
-    assert all(st == bs.OK for st, _ in res)
+    bad = [(i, st, cnt) for i, (st, cnt) in enumerate(res) if st != bs.OK or cnt != spec[i][0]]
+    assert not bad, f"batched outcomes differ from OK for {len(bad)} arrays, first {bad[:4]}"
     ms = []
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
@@ -534,9 +535,9 @@ def run_served(args, ws, rank, local):
             time.sleep(t - now)
         tickets.append(srv.submit(k, mv, o))
     lats = []
-    for tk in tickets:
+    for i, tk in enumerate(tickets):
         st, cnt, lat = srv.wait(tk)
-        assert st == bs.OK
+        assert st == bs.OK and cnt == spec[i][1], f"request {i} (n={spec[i][1]}, M={spec[i][2]}): status {st}, count {cnt}"
         lats.append(lat)
     wall = time.perf_counter() - t0
     stats = srv.stats()

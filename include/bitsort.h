@@ -257,8 +257,11 @@ typedef struct bitsort_server bitsort_server_t;
 /* A continuous-batching sort server on `device`.  Requests are admitted in
  * arrival order while the bytes their bitmap and output need
  * (ceil(M/8) + 4n, M = max_value + 1) fit in `budget_bytes`; admitted
- * requests are batched as they arrive and launched on up to
- * `max_inflight` concurrent streams, so that their device work overlaps. */
+ * requests are launched at once: a request of at least 2^22 keys alone as a
+ * plain sort, smaller ones together as batches of up to 64 MiB of work
+ * (8n + M/4 bytes each).  `max_inflight` streams (1..64) take the batches,
+ * each holding up to four queued behind one another, so that the device
+ * never waits for the scheduler and work on different streams overlaps. */
 bitsort_status_t bitsort_server_create(int device, uint64_t budget_bytes, int max_inflight,
                                        bitsort_server_t **server);
 

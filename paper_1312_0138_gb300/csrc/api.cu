@@ -289,32 +289,46 @@ bool bsx_ranges_overlap(const void *a, const void *b, uint64_t bytes) {
     return x < y + bytes && y < x + bytes;
 }
 
-bitsort_status_t bsx_ensure_part(bitsort_ctx *c, uint64_t n) {
-    if (c->part_cap >= n) return BITSORT_OK;
-    if (c->part) {
-        cudaDeviceSynchronize();
-        cudaFree(c->part);
-        c->part = nullptr;
-        c->part_cap = 0;
+// Grown on demand.  A context may be used from several streams, so growth
+// normally waits for the whole device before freeing the old buffer; a
+// context bound to one stream (c->stream_ordered, the server's) frees and
+// allocates in that stream's order instead, without stalling other streams.
+static cudaError_t regrow(bitsort_ctx *c, void **buf, size_t bytes, cudaStream_t s) {
+    if (c->stream_ordered) {
+        if (*buf) cudaFreeAsync(*buf, s);
+        *buf = nullptr;
+        return cudaMallocAsync(buf, bytes, s);
     }
-    cudaError_t e = cudaMalloc(&c->part, n * sizeof(uint32_t));
-    if (e != cudaSuccess) return bsx_check(e);
+    if (*buf) {
+        cudaDeviceSynchronize();
+        cudaFree(*buf);
+        *buf = nullptr;
+    }
+    return cudaMalloc(buf, bytes);
+}
+
+bitsort_status_t bsx_ensure_part(bitsort_ctx *c, uint64_t n, cudaStream_t s) {
+    if (c->part_cap >= n) return BITSORT_OK;
+    c->part_cap = 0;
+    cudaError_t e = regrow(c, reinterpret_cast<void **>(&c->part), n * sizeof(uint32_t), s);
+    if (e != cudaSuccess) {
+        c->part = nullptr;
+        return bsx_check(e);
+    }
     c->part_cap = n;
     return BITSORT_OK;
 }
 
-static bitsort_status_t ensure_bitmap(bitsort_ctx *c, uint64_t M) {
+static bitsort_status_t ensure_bitmap(bitsort_ctx *c, uint64_t M, cudaStream_t s) {
     const uint64_t words = (ceil_div(M, 32) + 3) / 4 * 4;
     if (c->bitmap_words >= words) return BITSORT_OK;
-    if (c->bitmap) {
-        cudaDeviceSynchronize();
-        cudaFree(c->bitmap);
+    c->bitmap_words = 0;
+    cudaError_t e = regrow(c, reinterpret_cast<void **>(&c->bitmap), words * 4, s);
+    if (e != cudaSuccess) {
         c->bitmap = nullptr;
-        c->bitmap_words = 0;
+        return bsx_check(e);
     }
-    cudaError_t e = cudaMalloc(&c->bitmap, words * 4);
-    if (e != cudaSuccess) return bsx_check(e);
-    e = cudaMemset(c->bitmap, 0, words * 4);
+    e = c->stream_ordered ? cudaMemsetAsync(c->bitmap, 0, words * 4, s) : cudaMemset(c->bitmap, 0, words * 4);
     if (e != cudaSuccess) return bsx_check(e);
     c->bitmap_words = words;
     return BITSORT_OK;
@@ -386,12 +400,12 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     a.bias = bias;
     bool alias = keys == out;
     if (cfg.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
-        bitsort_status_t st = bsx_ensure_part(c, (uint64_t)a.nslices * a.cap);
+        bitsort_status_t st = bsx_ensure_part(c, (uint64_t)a.nslices * a.cap, stream);
         if (st != BITSORT_OK) return st;
         a.part = c->part;
     } else if (cfg.path == BITSORT_PATH_PARTITION) {
         if (alias) {
-            bitsort_status_t st = bsx_ensure_part(c, n);
+            bitsort_status_t st = bsx_ensure_part(c, n, stream);
             if (st != BITSORT_OK) return st;
             a.part = c->part;
         } else {
@@ -399,7 +413,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         }
     }
     if (cfg.path == BITSORT_PATH_GLOBAL) {
-        bitsort_status_t st = ensure_bitmap(c, M);
+        bitsort_status_t st = ensure_bitmap(c, M, stream);
         if (st != BITSORT_OK) return st;
         a.bitmap = c->bitmap;
     }

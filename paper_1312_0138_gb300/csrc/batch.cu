@@ -82,7 +82,7 @@ static bsx_config batch_config(bitsort_ctx *c, uint64_t n, uint64_t M, int threa
 
 bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, size_t count,
                                    bitsort_result_t *d_results_user, cudaStream_t stream, bool async_alloc,
-                                   bitsort_batch_plan **out) {
+                                   bitsort_batch_plan **out, void *staging, size_t staging_cap) {
     *out = nullptr;
     if (count == 0 || !descs || count > (1u << 24)) return BITSORT_ERR_INVALID;
     for (size_t i = 0; i < count; ++i) {
@@ -218,10 +218,17 @@ bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, siz
         }
         a.result = d_results_user ? d_results_user + i : pl->d_results + i;
     }
-    std::vector<char> host(tables_bytes, 0);
-    memcpy(host.data() + off_arrays, arr.data(), count * sizeof(ArrayDesc));
-    memcpy(host.data() + off_segs, segs.data(), segs.size() * sizeof(Segment));
-    if (async_alloc) {
+    const bool use_staging = async_alloc && staging && staging_cap >= tables_bytes;
+    std::vector<char> host(use_staging ? 0 : tables_bytes, 0);
+    char *hb = use_staging ? (char *)staging : host.data();
+    memset(hb, 0, tables_bytes);
+    memcpy(hb + off_arrays, arr.data(), count * sizeof(ArrayDesc));
+    memcpy(hb + off_segs, segs.data(), segs.size() * sizeof(Segment));
+    if (use_staging) {
+        // pinned staging that the caller keeps until the stream has passed this copy
+        e = cudaMemcpyAsync(pl->tables, hb, tables_bytes, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(pl->scratch, 0, pl->scratch_bytes, stream);
+    } else if (async_alloc) {
         e = cudaMemcpyAsync(pl->tables, host.data(), tables_bytes, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(pl->scratch, 0, pl->scratch_bytes, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // host staging buffer goes out of scope
@@ -253,7 +260,7 @@ extern "C" bitsort_status_t bitsort_batch_plan_create(bitsort_ctx_t *c, const bi
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;
-    return bsx_plan_build(c, descs, count, nullptr, nullptr, false, plan);
+    return bsx_plan_build(c, descs, count, nullptr, nullptr, false, plan, nullptr, 0);
 }
 
 bitsort_status_t bsx_plan_launch_direct(bitsort_batch_plan *pl, cudaStream_t s) {
@@ -353,7 +360,7 @@ extern "C" bitsort_status_t bitsort_batched(bitsort_ctx_t *c, const bitsort_desc
     if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     bitsort_batch_plan *pl = nullptr;
-    bitsort_status_t st = bsx_plan_build(c, descs, count, d_results, s, true, &pl);
+    bitsort_status_t st = bsx_plan_build(c, descs, count, d_results, s, true, &pl, nullptr, 0);
     if (st != BITSORT_OK) return st;
     st = bsx_plan_launch_direct(pl, s);
     bsx_plan_release_async(pl, s);
@@ -418,7 +425,7 @@ extern "C" bitsort_status_t bitsort_batch_autotune(bitsort_ctx_t *c, const bitso
                     b.wpl = wpl;
                     c->batch = b;
                     bitsort_batch_plan *pl = nullptr;
-                    if (bsx_plan_build(c, descs, count, nullptr, nullptr, false, &pl) != BITSORT_OK) continue;
+                    if (bsx_plan_build(c, descs, count, nullptr, nullptr, false, &pl, nullptr, 0) != BITSORT_OK) continue;
                     bool ok = bsx_plan_launch_direct(pl, s) == BITSORT_OK;   // warm-up
                     float ms = 0, sum = 0;
                     for (int r = 0; r < 3 && ok; ++r) {

@@ -52,6 +52,7 @@ struct bitsort_ctx {
     uint64_t bitmap_words = 0;
     void *flush = nullptr;        // L2 flush buffer for tuning
     size_t flush_bytes = 0;
+    bool stream_ordered = false;  // used from one stream only: buffers regrow in its order
 
     // multiset path (msort.cu): look-back words tagged with a pass epoch
     // (never cleared between passes) and a small block cleared per call
@@ -106,14 +107,14 @@ bool bsx_ranges_overlap(const void *a, const void *b, uint64_t bytes);
 int bsx_grid_for(bitsort_ctx *c, int threads, uint32_t smem, uint32_t items);
 bitsort_status_t bsx_validate(const uint32_t *keys, uint64_t n, uint32_t max_value, const uint32_t *out);
 bitsort_status_t bsx_reset_scratch(bitsort_ctx *c);
-bitsort_status_t bsx_ensure_part(bitsort_ctx *c, uint64_t n);
+bitsort_status_t bsx_ensure_part(bitsort_ctx *c, uint64_t n, cudaStream_t s);
 void bsx_multiset_free(bitsort_ctx *c);
 void bsx_widths_free(bitsort_ctx *c);
 
 // batch plans (batch.cu)
 bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, size_t count,
                                 bitsort_result_t *d_results_user, cudaStream_t stream, bool async_alloc,
-                                bitsort_batch_plan **out);
+                                bitsort_batch_plan **out, void *staging = nullptr, size_t staging_cap = 0);
 bitsort_status_t bsx_plan_launch_direct(bitsort_batch_plan *pl, cudaStream_t s);
 void bsx_plan_release_async(bitsort_batch_plan *pl, cudaStream_t s);
 const bitsort_result_t *bsx_plan_results_ptr(const bitsort_batch_plan *pl);

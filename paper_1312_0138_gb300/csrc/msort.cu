@@ -406,7 +406,7 @@ bitsort_status_t multiset_run(bitsort_ctx *c, const uint32_t *keys, uint64_t n, 
     // so the parity shifts and a copy ends the sort
     const bool copy_back = inplace && (P & 1u);
     if (P > 1 || inplace) {
-        if ((st = bsx_ensure_part(c, n)) != BITSORT_OK) return st;
+        if ((st = bsx_ensure_part(c, n, s)) != BITSORT_OK) return st;
     }
     uint32_t *tmp = c->part;
     if (c->ms_epoch + P > kEpochMax) {   // epochs wrap: start the look-back array afresh

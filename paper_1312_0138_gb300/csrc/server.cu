@@ -5,12 +5,17 @@
 //   * requests wait in arrival order; the head request is admitted while the
 //     bytes its bitmap and output need, ceil(M/8) + 4n, fit in what is left of
 //     the budget (strict FIFO, so a large request is never starved);
-//   * whenever one of `max_inflight` slots (a stream and a context each) is
-//     free and admitted requests are waiting, they are launched on that
-//     slot's stream: requests of at least kPlainMinKeys keys each as one
-//     plain sort (one kernel per phase, every SM), the smaller ones together
-//     as one batch (one persistent launch); work launched while other slots
-//     run overlaps with it on the device;
+//   * admitted work is launched at once as batches: a request of at least
+//     kPlainMinKeys keys alone, as one plain sort (one kernel per phase,
+//     every SM), or else the run of smaller requests at the head, up to
+//     kBatchQuantum bytes of work, as one batch (one persistent launch);
+//   * `max_inflight` streams, each with its own context, take the batches
+//     (large requests on stream 0, one after another; small-request batches
+//     on the others); a stream holds up to kDepth batches queued, so the
+//     device always has the next batch in its queue while the scheduler
+//     prepares more, and work on different streams overlaps on the device;
+//     a stream that still has work queued takes only full batches, so that
+//     small requests gather into few launches while the device is busy;
 //   * a finished batch (its event has completed) releases its budget, and its
 //     requests' outcomes (copied to pinned host memory behind the kernel) are
 //     handed to the waiters together with their latency, measured from
@@ -48,21 +53,32 @@ struct Request {
     double latency = 0;
 };
 
-struct Slot {
+struct Lane {                     // one stream and the context of its plain sorts
     cudaStream_t stream = nullptr;
+    bitsort_ctx *ctx = nullptr;
+    uint32_t queued = 0;             // batches launched on it and not yet finished
+};
+
+struct Batch {                    // one launched unit of work and its outcome buffers
+    int lane = -1;
     cudaEvent_t done = nullptr;
-    bitsort_ctx *ctx = nullptr;                // scratch of this slot's plain sorts
     bitsort_result_t *dev_results = nullptr;   // kMaxBatch outcomes on the device
     bitsort_result_t *host_results = nullptr;  // pinned
-    size_t host_cap = 0;
+    void *staging = nullptr;                   // pinned host copy of the batch plan's tables
+    size_t staging_cap = 0;
     bool busy = false;
+    uint64_t seq = 0;                          // launch order (finished in order per lane)
     std::vector<uint64_t> tickets;
-    uint64_t bytes = 0;
 };
 
 constexpr size_t kMaxBatch = 1024;
-constexpr uint64_t kPlainMinKeys = 1ull << 20;   // requests this large run as plain sorts
+constexpr uint64_t kPlainMinKeys = 1ull << 22;   // requests this large run as plain sorts
+constexpr uint64_t kBatchQuantum = 64ull << 20;  // work bytes (8n + M/4) of one batch of small requests
+constexpr size_t kStagingBytes = 1u << 20;       // pinned table staging per batch (larger plans stage on their own)
+constexpr uint32_t kDepth = 4;                   // batches queued per stream of small-request batches
+constexpr uint32_t kDepthLarge = 16;             // plain sorts queued on stream 0
 
+uint64_t work_bytes(uint64_t n, uint32_t max_value) { return 8 * n + ((uint64_t)max_value + 1) / 4; }
 uint64_t request_bytes(uint64_t n, uint32_t max_value) {
     const uint64_t M = (uint64_t)max_value + 1;
     return (M + 7) / 8 + 4 * n;
@@ -75,10 +91,11 @@ struct bitsort_server {
     uint64_t budget = 0;
     uint64_t in_use = 0;
     bitsort_ctx *ctx = nullptr;
-    std::vector<Slot> slots;
+    std::vector<Lane> lanes;
+    std::vector<Batch> pool;
     std::deque<uint64_t> waiting;
     std::unordered_map<uint64_t, Request> reqs;
-    uint64_t next_ticket = 1;
+    uint64_t next_ticket = 1, next_seq = 1;
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::thread thread;
@@ -87,68 +104,60 @@ struct bitsort_server {
     uint64_t completed = 0, keys = 0, batches = 0, max_concurrent = 0;
 
     void run();
-    bool launch_batch(Slot &s, std::vector<uint64_t> &batch);
-    void finish_batch(Slot &s);
+    bool launch_batch(Batch &b, const std::vector<bitsort_desc_t> &jobs);
+    void finish_batch(Batch &b);
 };
 
-bool bitsort_server::launch_batch(Slot &s, std::vector<uint64_t> &batch) {
-    if (!s.host_results) {
-        if (cudaMallocHost(&s.host_results, kMaxBatch * sizeof(bitsort_result_t)) != cudaSuccess) return false;
-        s.host_cap = kMaxBatch;
+// Launches one batch on its stream.  Runs without the server lock: it reads
+// only `jobs` (copied under the lock) and state that the scheduler thread
+// alone touches (the batch record, the streams, the scheduler's context).
+bool bitsort_server::launch_batch(Batch &b, const std::vector<bitsort_desc_t> &jobs) {
+    if (!b.host_results) {
+        if (cudaMallocHost(&b.host_results, kMaxBatch * sizeof(bitsort_result_t)) != cudaSuccess) return false;
     }
-    // large requests first (plain sorts), then the small ones (one batch);
-    // outcome i of the slot belongs to ticket i of the reordered list
-    std::stable_partition(batch.begin(), batch.end(), [&](uint64_t t) { return reqs[t].n >= kPlainMinKeys; });
-    size_t nplain = 0;
-    while (nplain < batch.size() && reqs[batch[nplain]].n >= kPlainMinKeys) ++nplain;
+    if (!b.staging) {
+        if (cudaMallocHost(&b.staging, kStagingBytes) != cudaSuccess) return false;
+        b.staging_cap = kStagingBytes;
+    }
+    Lane &ln = lanes[b.lane];
     bitsort_status_t st = BITSORT_OK;
-    if (nplain < batch.size()) {
-        std::vector<bitsort_desc_t> descs(batch.size() - nplain);
-        for (size_t i = nplain; i < batch.size(); ++i) {
-            const Request &r = reqs[batch[i]];
-            bitsort_desc_t &d = descs[i - nplain];
-            d.keys = r.keys;
-            d.out = r.out;
-            d.n = r.n;
-            d.max_value = r.max_value;
-            d.reserved = 0;
-        }
+    const bitsort_desc_t &j0 = jobs[0];
+    if (jobs.size() == 1 && j0.n >= kPlainMinKeys) {
+        st = bitsort_ex(ln.ctx, j0.keys, j0.n, j0.max_value, j0.out, b.dev_results,
+                        reinterpret_cast<bitsort_stream_t>(ln.stream));
+    } else {
         bitsort_batch_plan *pl = nullptr;
-        st = bsx_plan_build(ctx, descs.data(), descs.size(), s.dev_results + nplain, s.stream, true, &pl);
+        st = bsx_plan_build(ctx, jobs.data(), jobs.size(), b.dev_results, ln.stream, true, &pl, b.staging,
+                            b.staging_cap);
         if (st != BITSORT_OK) return false;
-        st = bsx_plan_launch_direct(pl, s.stream);
-        bsx_plan_release_async(pl, s.stream);
+        st = bsx_plan_launch_direct(pl, ln.stream);
+        bsx_plan_release_async(pl, ln.stream);
     }
-    for (size_t i = 0; i < nplain && st == BITSORT_OK; ++i) {
-        const Request &r = reqs[batch[i]];
-        st = bitsort_ex(s.ctx, r.keys, r.n, r.max_value, r.out, s.dev_results + i,
-                        reinterpret_cast<bitsort_stream_t>(s.stream));
-    }
-    cudaMemcpyAsync(s.host_results, s.dev_results, batch.size() * sizeof(bitsort_result_t), cudaMemcpyDeviceToHost,
-                    s.stream);
-    cudaEventRecord(s.done, s.stream);
-    s.tickets = batch;
-    s.busy = true;
-    ++batches;
+    cudaMemcpyAsync(b.host_results, b.dev_results, jobs.size() * sizeof(bitsort_result_t), cudaMemcpyDeviceToHost,
+                    ln.stream);
+    cudaEventRecord(b.done, ln.stream);
+    b.seq = next_seq++;
+    ++ln.queued;
     return st == BITSORT_OK;
 }
 
-void bitsort_server::finish_batch(Slot &s) {
+void bitsort_server::finish_batch(Batch &b) {
     const auto now = clock_type::now();
-    for (size_t i = 0; i < s.tickets.size(); ++i) {
-        auto it = reqs.find(s.tickets[i]);
+    for (size_t i = 0; i < b.tickets.size(); ++i) {
+        auto it = reqs.find(b.tickets[i]);
         if (it == reqs.end()) continue;
         Request &r = it->second;
-        r.status = (bitsort_status_t)s.host_results[i].status;
-        r.count = s.host_results[i].count;
+        r.status = (bitsort_status_t)b.host_results[i].status;
+        r.count = b.host_results[i].count;
         r.latency = std::chrono::duration<double>(now - r.submitted).count();
         r.done = true;
         in_use -= r.bytes;
         ++completed;
         keys += r.n;
     }
-    s.tickets.clear();
-    s.busy = false;
+    b.tickets.clear();
+    b.busy = false;
+    --lanes[b.lane].queued;
 }
 
 void bitsort_server::run() {
@@ -157,32 +166,85 @@ void bitsort_server::run() {
     for (;;) {
         bool progressed = false;
         uint64_t busy = 0;
-        for (Slot &s : slots) {
-            if (s.busy && cudaEventQuery(s.done) == cudaSuccess) {
-                finish_batch(s);
+        for (Batch &b : pool) {
+            if (b.busy && cudaEventQuery(b.done) == cudaSuccess) {
+                finish_batch(b);
                 progressed = true;
             }
-            busy += s.busy ? 1 : 0;
+            busy += b.busy ? 1 : 0;
         }
         if (progressed) cv_done.notify_all();
-        size_t free_slots = 0;
-        for (Slot &s : slots) free_slots += s.busy ? 0 : 1;
-        for (Slot &s : slots) {
-            if (s.busy || waiting.empty()) continue;
-            // an even share of the waiting requests per free slot, so that a
-            // burst spreads over the slots and overlaps on the device
-            const size_t share = std::min(kMaxBatch, (waiting.size() + free_slots - 1) / std::max<size_t>(1, free_slots));
-            --free_slots;
+        while (!waiting.empty()) {
+            // a free batch record and the stream with the fewest queued batches
+            Batch *b = nullptr;
+            for (Batch &x : pool)
+                if (!x.busy) {
+                    b = &x;
+                    break;
+                }
+            // large requests run one after another on stream 0, as a plain
+            // caller's would (concurrent large sorts only contend for the L2
+            // that each one's partition pass fills for its bucket pass);
+            // batches of small requests take the least loaded other stream
+            const bool head_large = reqs[waiting.front()].n >= kPlainMinKeys;
+            const int first = (!head_large && lanes.size() > 1) ? 1 : 0;
+            const int last = head_large ? 1 : (int)lanes.size();
+            int lane = -1;
+            for (int i = first; i < last; ++i) {
+                const uint32_t depth = (i == 0 && lanes.size() > 1) ? kDepthLarge : kDepth;
+                if (lanes[i].queued < depth && (lane < 0 || lanes[i].queued < lanes[lane].queued)) lane = i;
+            }
+            if (!b || lane < 0) break;
+            if (lanes[lane].queued > 0) {
+                // the device has work: launch only a full batch (a large
+                // request, or small ones worth a quantum), so that small
+                // requests gather into few launches; an idle stream takes
+                // whatever is waiting
+                bool full = false;
+                uint64_t w = 0;
+                size_t k = 0;
+                for (auto it = waiting.begin(); it != waiting.end() && !full; ++it) {
+                    const Request &r = reqs[*it];
+                    w += work_bytes(r.n, r.max_value);
+                    full = r.n >= kPlainMinKeys || w >= kBatchQuantum || ++k >= kMaxBatch;
+                }
+                if (!full) break;
+            }
+            // the head request alone if it is large, else the run of small
+            // requests at the head up to one quantum of work (FIFO admission)
             std::vector<uint64_t> batch;
-            while (!waiting.empty() && batch.size() < share) {
+            uint64_t work = 0;
+            while (!waiting.empty() && batch.size() < kMaxBatch) {
                 Request &r = reqs[waiting.front()];
+                const bool large = r.n >= kPlainMinKeys;
+                if (large && !batch.empty()) break;
                 if (in_use + r.bytes > budget) break;
                 in_use += r.bytes;
                 batch.push_back(waiting.front());
                 waiting.pop_front();
+                work += work_bytes(r.n, r.max_value);
+                if (large || work >= kBatchQuantum) break;
             }
             if (batch.empty()) break;
-            if (!launch_batch(s, batch)) {
+            std::vector<bitsort_desc_t> jobs(batch.size());
+            for (size_t i = 0; i < batch.size(); ++i) {
+                const Request &r = reqs[batch[i]];
+                jobs[i].keys = r.keys;
+                jobs[i].out = r.out;
+                jobs[i].n = r.n;
+                jobs[i].max_value = r.max_value;
+                jobs[i].reserved = 0;
+            }
+            b->lane = lane;
+            b->tickets = batch;
+            b->busy = true;   // reserved: only this thread finishes batches
+            // launch without the lock, so that submissions are not held up
+            lk.unlock();
+            const uint32_t before = lanes[lane].queued;
+            const bool ok = launch_batch(*b, jobs);
+            lk.lock();
+            ++batches;
+            if (!ok) {
                 fatal = BITSORT_ERR_CUDA;
                 for (uint64_t t : batch) {
                     Request &r = reqs[t];
@@ -190,7 +252,9 @@ void bitsort_server::run() {
                     r.done = true;
                     in_use -= r.bytes;
                 }
-                s.busy = false;
+                if (lanes[lane].queued > before) --lanes[lane].queued;
+                b->busy = false;
+                b->tickets.clear();
                 cv_done.notify_all();
                 continue;
             }
@@ -201,8 +265,10 @@ void bitsort_server::run() {
         if (stop && waiting.empty() && busy == 0) break;
         if (!progressed) {
             if (busy > 0) {
+                // a timed sleep lasts tens of microseconds (timer slack): poll
+                // the batches' events between yields while work is in flight
                 lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(5));
+                std::this_thread::yield();
                 lk.lock();
             } else {
                 cv_sched.wait_for(lk, std::chrono::milliseconds(2));
@@ -224,12 +290,27 @@ extern "C" bitsort_status_t bitsort_server_create(int device, uint64_t budget_by
     }
     sv->device = device;
     sv->budget = budget_bytes;
-    sv->slots.resize(max_inflight);
-    for (Slot &s : sv->slots) {
-        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
-            bitsort_ctx_create(device, &s.ctx) != BITSORT_OK ||
-            cudaMalloc(&s.dev_results, kMaxBatch * sizeof(bitsort_result_t)) != cudaSuccess) {
+    // batch plans allocate their tables and scratch stream-ordered: keep the
+    // device's pool from handing that memory back to the system at every
+    // synchronisation (its default), which would make each plan allocate anew
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    sv->lanes.resize(max_inflight);
+    for (Lane &ln : sv->lanes) {
+        if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            bitsort_ctx_create(device, &ln.ctx) != BITSORT_OK) {
+            bitsort_server_destroy(sv);
+            return BITSORT_ERR_CUDA;
+        }
+        ln.ctx->stream_ordered = true;   // used on this stream only
+    }
+    sv->pool.resize((size_t)max_inflight * kDepth + kDepthLarge);
+    for (Batch &b : sv->pool) {
+        if (cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&b.dev_results, kMaxBatch * sizeof(bitsort_result_t)) != cudaSuccess) {
             bitsort_server_destroy(sv);
             return BITSORT_ERR_CUDA;
         }
@@ -298,13 +379,17 @@ extern "C" bitsort_status_t bitsort_server_destroy(bitsort_server_t *sv) {
     }
     if (sv->thread.joinable()) sv->thread.join();
     cudaSetDevice(sv->device);
-    for (Slot &s : sv->slots) {
-        if (s.stream) cudaStreamSynchronize(s.stream);
-        if (s.done) cudaEventDestroy(s.done);
-        if (s.stream) cudaStreamDestroy(s.stream);
-        if (s.host_results) cudaFreeHost(s.host_results);
-        if (s.dev_results) cudaFree(s.dev_results);
-        if (s.ctx) bitsort_ctx_destroy(s.ctx);
+    for (Lane &ln : sv->lanes)
+        if (ln.stream) cudaStreamSynchronize(ln.stream);
+    for (Batch &b : sv->pool) {
+        if (b.done) cudaEventDestroy(b.done);
+        if (b.host_results) cudaFreeHost(b.host_results);
+        if (b.staging) cudaFreeHost(b.staging);
+        if (b.dev_results) cudaFree(b.dev_results);
+    }
+    for (Lane &ln : sv->lanes) {
+        if (ln.stream) cudaStreamDestroy(ln.stream);
+        if (ln.ctx) bitsort_ctx_destroy(ln.ctx);
     }
     if (sv->ctx) bitsort_ctx_destroy(sv->ctx);
     delete sv;
