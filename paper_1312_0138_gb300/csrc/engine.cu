@@ -796,25 +796,46 @@ __device__ void part_tile(const ArrayDesc &a, const uint32_t (&x)[kKeysPerThread
     } else {
         __syncthreads();   // (the histogram pass reports keys above max_value)
     }
-    // reserve each bucket's run (needs the counts), then turn counts into prefixes
-    for (uint32_t i = threadIdx.x; i < nbins; i += T) {
-        const uint32_t c = hist[i];
-        uint32_t start = 0, fit = 0;
-        if (c && i < nb) {
-            const uint32_t at = atomicAdd(&a.cursor[i], c);
-            if (capacity) {
-                const uint64_t cap = a.cap;
-                start = (uint32_t)((uint64_t)i * cap + at);
-                fit = at >= cap ? 0u : (uint32_t)min((uint64_t)c, cap - at);
-                if (fit < c) atomicOr(&a.sync[SY_OVERFLOW], 1u);   // only with repeated keys
-            } else {
-                const uint64_t st = __ldcg(&a.offsets[i]) + at;
-                start = (uint32_t)st;
-                fit = st >= a.n ? 0u : (uint32_t)min((uint64_t)c, a.n - st);   // a sane scratch never clips
-            }
+    // reserve each bucket's run (needs the counts), then turn counts into
+    // prefixes.  A thread owns up to kReserve bins per round and issues
+    // their global atomics (and offset loads) before it uses any result, so
+    // a wide fan-out waits for one atomic round trip per round, not per bin.
+    constexpr int kReserve = 4;
+    for (uint32_t r0 = 0; r0 < nbins; r0 += kReserve * T) {
+        uint32_t cnt[kReserve], at[kReserve];
+#pragma unroll
+        for (int u = 0; u < kReserve; ++u) {
+            const uint32_t i = r0 + u * T + threadIdx.x;
+            cnt[u] = i < nb ? hist[i] : 0u;
         }
-        delta[i] = start;
-        lim[i] = fit;
+#pragma unroll
+        for (int u = 0; u < kReserve; ++u)
+            at[u] = cnt[u] ? atomicAdd(&a.cursor[r0 + u * T + threadIdx.x], cnt[u]) : 0u;
+        uint64_t off[kReserve];
+#pragma unroll
+        for (int u = 0; u < kReserve; ++u)
+            off[u] = (!capacity && cnt[u]) ? __ldcg(&a.offsets[r0 + u * T + threadIdx.x]) : 0ull;
+#pragma unroll
+        for (int u = 0; u < kReserve; ++u) {
+            const uint32_t i = r0 + u * T + threadIdx.x;
+            if (i >= nbins) break;
+            const uint32_t c = cnt[u];
+            uint32_t start = 0, fit = 0;
+            if (c) {
+                if (capacity) {
+                    const uint64_t cap = a.cap;
+                    start = (uint32_t)((uint64_t)i * cap + at[u]);
+                    fit = at[u] >= cap ? 0u : (uint32_t)min((uint64_t)c, cap - at[u]);
+                    if (fit < c) atomicOr(&a.sync[SY_OVERFLOW], 1u);   // only with repeated keys
+                } else {
+                    const uint64_t st = off[u] + at[u];
+                    start = (uint32_t)st;
+                    fit = st >= a.n ? 0u : (uint32_t)min((uint64_t)c, a.n - st);   // a sane scratch never clips
+                }
+            }
+            delta[i] = start;
+            lim[i] = fit;
+        }
     }
     block_exclusive_scan_u32<T>(nbins, hist, hist, m);
     for (uint32_t i = threadIdx.x; i < nbins; i += T) {
