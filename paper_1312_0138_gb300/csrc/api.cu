@@ -105,7 +105,8 @@ extern "C" bitsort_status_t bitsort_ctx_create(int device, bitsort_ctx_t **out) 
     // dynamic shared memory available next to the kernel's static block
     c->smem_optin = (uint32_t)prop.sharedMemPerBlockOptin - 1024;
     c->wait_limit_ns = kDefaultWaitNs;
-    if (engine_set_smem_limit(256, c->smem_optin) != 0 || engine_set_smem_limit(512, c->smem_optin) != 0) {
+    if (engine_set_smem_limit(256, c->smem_optin) != 0 || engine_set_smem_limit(512, c->smem_optin) != 0 ||
+        engine_set_smem_limit(1024, c->smem_optin) != 0) {
         delete c;
         return BITSORT_ERR_CUDA;
     }
@@ -224,7 +225,8 @@ bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M) {
 // Make a configuration valid for (n, M): the slice count within bounds, the
 // slice a multiple of 128 values, FUSED only where one slice covers M.
 bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
-    if (cfg.threads != 256 && cfg.threads != 512) cfg.threads = 512;
+    if (cfg.threads != 256 && cfg.threads != 512 && cfg.threads != 1024) cfg.threads = 512;
+    if (cfg.threads == 1024 && cfg.persistent) cfg.threads = 512;   // the persistent engine has 256 / 512
     if (cfg.wpl != 1 && cfg.wpl != 2 && cfg.wpl != 4 && cfg.wpl != 8) cfg.wpl = 2;
     if (cfg.stage && cfg.wpl == 2) cfg.wpl = 1;    // staged emission: 1, 4 or 8 words per lane
     if (!cfg.stage && cfg.wpl == 8) cfg.wpl = 4;   // direct emission: 1, 2 or 4
@@ -467,9 +469,31 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         return BITSORT_OK;
     }
     // one kernel per phase, each at the occupancy its shared memory allows;
-    // later phases use programmatic dependent launch to hide the launch gap
+    // later phases use programmatic dependent launch to hide the launch gap.
+    // A 512-thread plan runs two phases at 1024 threads (one CTA per SM)
+    // where that measured faster on GB300: the partition with a wide fan-out
+    // (its tile doubles to 16 Ki keys, so the per-bucket work of a tile is
+    // spread over twice the keys: 16.0 -> 12.6 ms at 4096 buckets, n = 2^31),
+    // and the bucket phase when every SM works through many slices without
+    // staging (255.9 -> 212.0 us for 4096 sparse slices, n = 2^24); with
+    // staging, or one or two slices per SM, 512 threads stay faster.
+    int Tp = T, Tb = T;
+    if (T == 512 && a.path == BITSORT_PATH_PARTITION) {
+        const bool bulk_part = ((uintptr_t)keys & 15u) == 0 && cfg.stream_part;   // streaming partition stays
+        if (a.nslices >= 1024 && !bulk_part &&
+            part_smem_bytes(a.nslices, (uint32_t)(kKeysPerThread * 1024)) <= c->smem_optin)
+            Tp = 1024;
+        if (!cfg.stage && cfg.emit == EMIT_WORD && a.nslices >= 4u * (uint32_t)c->sms &&
+            slice_smem_bytes(cfg.S, 1024, false) <= c->smem_optin)
+            Tb = 1024;
+    }
+    if (Tp != T) {
+        a.tile_keys = (uint32_t)(kKeysPerThread * Tp);
+        a.key_tiles = (uint32_t)ceil_div(n, (uint64_t)a.tile_keys);
+    }
     int launched = 0;
     auto phase = [&](int kind, uint32_t items, uint32_t smem) -> bool {
+        const int Tk = (kind == IT_HIST || kind == IT_PART || kind == IT_PARTS) ? Tp : kind == IT_BUCKET ? Tb : T;
         if (items == 0) return true;
         if (smem > c->smem_optin) {
             bsx_note_error((int)cudaErrorInvalidValue, "shared memory above the per-block limit");
@@ -482,13 +506,13 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
             c->tkind[launched] = kind;
         }
         int per_sm = 1;
-        if (kernel_max_blocks_per_sm(kind, T, smem, &per_sm) != 0 || per_sm < 1) per_sm = 1;
+        if (kernel_max_blocks_per_sm(kind, Tk, smem, &per_sm) != 0 || per_sm < 1) per_sm = 1;
         // slice phases and the streaming HIST / GSCATTER / PARTS phases: one
         // wave of resident CTAs; PART: a few tiles per CTA
         const bool one_wave = kind != IT_PART;
         uint64_t grid = (uint64_t)c->sms * (uint64_t)per_sm * (one_wave ? 1u : 8u);
         if (grid > items) grid = items;
-        int e = kernel_launch(kind, q, T, smem, (int)grid, stream, launched > 0);
+        int e = kernel_launch(kind, q, Tk, smem, (int)grid, stream, launched > 0);
         if (e != 0) {
             bsx_note_error(e, "phase kernel launch");
             return false;
@@ -501,7 +525,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         return true;
     };
     const uint32_t sl = cfg.emit == EMIT_RANK ? rank_smem_bytes(cfg.S, a.stage_cap)
-                                              : slice_smem_bytes(cfg.S, T, cfg.stage);
+                                              : slice_smem_bytes(cfg.S, Tb, cfg.stage);
     bool ok = true;
     if (a.path == BITSORT_PATH_FUSED) {
         ok = phase(IT_BUCKET, 1, sl);
@@ -894,7 +918,7 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
                    "\"summary\": %d, \"ms\": %lf",
                    &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &emit, &pstream, &summary, &ms) != 13)
             return BITSORT_ERR_INVALID;
-        if (p < 1 || p > 3 || (th != 256 && th != 512) || ln < 0 || ln > 64 || lm < 0 || lm > 33)
+        if (p < 1 || p > 3 || (th != 256 && th != 512 && th != 1024) || ln < 0 || ln > 64 || lm < 0 || lm > 33)
             return BITSORT_ERR_INVALID;
         bsx_config cfg;
         cfg.path = (bitsort_path_t)p;

@@ -1520,12 +1520,24 @@ static KernelFn kernel_for(int kind, int threads) {
             case IT_GSCAN: return phase_kernel<512, IT_GSCAN>;
             case IT_PARTS: return phase_kernel<512, IT_PARTS>;
         }
+    } else if (threads == 1024) {
+        // one CTA per SM for the phase kernels of a single sort (the
+        // persistent engine stays at 256 / 512 threads)
+        switch (kind) {
+            case IT_HIST: return phase_kernel<1024, IT_HIST>;
+            case IT_PART: return phase_kernel<1024, IT_PART>;
+            case IT_BUCKET: return phase_kernel<1024, IT_BUCKET>;
+            case IT_GSCATTER: return phase_kernel<1024, IT_GSCATTER>;
+            case IT_GSCAN: return phase_kernel<1024, IT_GSCAN>;
+            case IT_PARTS: return phase_kernel<1024, IT_PARTS>;
+        }
     }
     return nullptr;
 }
 
 int engine_set_smem_limit(int threads, uint32_t smem_bytes) {
     for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN, (int)IT_PARTS}) {
+        if (kind == -1 && threads == 1024) continue;   // no persistent engine at 1024 threads
         KernelFn f = kernel_for(kind, threads);
         if (!f) return (int)cudaErrorInvalidValue;
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
