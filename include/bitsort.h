@@ -161,7 +161,7 @@ bitsort_status_t bitsort_u64(bitsort_ctx_t *ctx, const uint64_t *keys, uint64_t 
  *     Reported through d_result (DEVICE, nullable = the context) like
  *     bitsort_ex().
  *   - Scratch (grown on demand, owned by the context): a buffer of n keys
- *     (shared with the bitmap path), ceil(n / 4096) x 2^split_bits look-back
+ *     (shared with the bitmap path), ceil(n / 8192) x 2^split_bits look-back
  *     words and a 4.4 KB block.  Calls on one context are stream-ordered on
  *     the stream they are given: do not run two at once on one context. */
 bitsort_status_t bitsort_multiset(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n, uint32_t max_value,

@@ -38,7 +38,7 @@ namespace {
 using namespace bsx;
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kT = 256;                  // threads of a tile
+constexpr int kT = 512;                  // threads of a tile
 constexpr int kK = 16;                   // keys per thread
 constexpr uint32_t kTile = kT * kK;      // keys per tile
 constexpr int kNW = kT / 32;
@@ -211,10 +211,10 @@ __global__ void __launch_bounds__(kT) ms_hist_kernel(const uint32_t *keys, uint6
 
 // One stable split by the D bits at `shift`: tile `ticket` of the pass.
 template <int D>
-__global__ void __launch_bounds__(kT, 4) ms_pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(kT, 1024 / kT) ms_pass_kernel(PassArgs a) {
     constexpr uint32_t R = 1u << D;
     __shared__ uint32_t s_keys[kTile];
-    __shared__ uint32_t s_warp[kNW][R];   // keys of each group per warp, then the warp's offset in the group
+    __shared__ uint16_t s_warp[kNW][R];   // keys of each group per warp, then the warp's offset in the group (< tile)
     __shared__ uint32_t s_start[R];       // the group's count, then its start in the reordered tile
     __shared__ uint32_t s_base[R];        // output position of the group's first key in the tile, minus its start
     __shared__ uint32_t s_scan[kNW];
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kT, 4) ms_pass_kernel(PassArgs a) {
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.misc[kMiscTicket + a.pass], 1u);
-    for (uint32_t i = threadIdx.x; i < (uint32_t)kNW * R; i += kT) (&s_warp[0][0])[i] = 0u;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kNW * R; i += kT) (&s_warp[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t t0 = (uint64_t)tile * kTile;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kT, 4) ms_pass_kernel(PassArgs a) {
         uint32_t old = 0;
         if (valid && below == 0) {   // the group's first lane adds the step's keys of the group
             old = s_warp[warp][g];
-            s_warp[warp][g] = old + __popc(peers);
+            s_warp[warp][g] = (uint16_t)(old + __popc(peers));
         }
         old = __shfl_sync(kFull, old, valid ? __ffs(peers) - 1 : lane);
         rk[j] = old + below;
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kT, 4) ms_pass_kernel(PassArgs a) {
 #pragma unroll
         for (int w = 0; w < kNW; ++w) {
             const uint32_t c = s_warp[w][g];
-            s_warp[w][g] = run;
+            s_warp[w][g] = (uint16_t)run;
             run += c;
         }
         s_start[g] = run;

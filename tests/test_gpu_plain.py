@@ -58,6 +58,11 @@ CONFIGS = [
     ("rank_exact_S4096_256", bs.PATH_PARTITION, 4096, 256, dict(layout=0, emit=1)),
     ("rank_exact_odd_persist", bs.PATH_PARTITION, 300_032, 512, dict(layout=0, emit=1, persistent=1)),
     ("rank_cap_S1M_persist", bs.PATH_PARTITION, 1 << 20, 256, dict(layout=1, emit=1, persistent=1)),
+    ("fused1024", bs.PATH_FUSED, 0, 1024, dict(words_per_lane=1)),
+    ("exact_S4096_1024", bs.PATH_PARTITION, 4096, 1024, dict(layout=0)),
+    ("cap_S64K_1024_w2", bs.PATH_PARTITION, 1 << 16, 1024, dict(layout=1, words_per_lane=2)),
+    ("global_S64K_1024", bs.PATH_GLOBAL, 1 << 16, 1024, {}),
+    ("exact_S1M_1024_stage", bs.PATH_PARTITION, 1 << 20, 1024, dict(layout=0, stage=1)),
     ("rank_fused", bs.PATH_FUSED, 0, 512, dict(emit=1)),
     ("global_S16K_w1", bs.PATH_GLOBAL, 1 << 14, 512, dict(words_per_lane=1)),
     ("global_S1M_256_w4", bs.PATH_GLOBAL, 1 << 20, 256, dict(words_per_lane=4)),
