@@ -455,7 +455,7 @@ def time_cub(keys, M, flush, stream, steps):
 
 
 def run_batched(args, ws, rank, local):
-    """configs[3]: 4096 arrays in one persistent launch (graph replay) vs the
+    """4096 arrays of uneven sizes and ranges in one persistent launch (graph replay) vs the
     same arrays as 4096 plain launches."""
     import torch
     import gen
@@ -521,7 +521,7 @@ def run_batched(args, ws, rank, local):
 
 
 def run_served(args, ws, rank, local):
-    """configs[4]: Poisson arrivals through the serving loop."""
+    """Poisson arrivals of sort requests of uneven sizes through the serving loop."""
     import torch
     import gen
     import paper_1312_0138_gb300 as bs

@@ -104,7 +104,7 @@ def test_rank_emission_falls_back_on_skewed_slices(ctx, layout):
     check(ctx, gen.shuffle(34, keys), (1 << 20) + 4096, path=bs.PATH_PARTITION, S=4096, layout=layout, emit=1)
 
 
-def test_config0_default_path(ctx):
+def test_default_plan_n100k_range_2e20(ctx):
     keys = gen.floyd(gen.SEED_BASE + 0, 100_000, 1 << 20)
     check(ctx, keys, (1 << 20) - 1)
 
