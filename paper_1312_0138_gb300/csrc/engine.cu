@@ -681,10 +681,11 @@ __device__ void slice_finish(const EngineParams &P, const ArrayDesc &a, uint32_t
     uint32_t w0, w1;
     slice_count<T>(P, a, s, bm, words, wpl, w0, w1, m);
     const uint64_t base = m.excl + m.wbase[warp];
-    uint32_t *stage = stage_all + warp * kStageWords;
-    if (a.stage && wpl == 8) emit_runs_staged<8>(bm, w0, w1, v0, base, a.out, a.n, stage, kStageWords);
-    else if (a.stage && wpl == 4) emit_runs_staged<4>(bm, w0, w1, v0, base, a.out, a.n, stage, kStageWords);
-    else if (a.stage) emit_words_staged(bm, w0, w1, v0, base, a.out, a.n, stage, kStageWords);
+    constexpr uint32_t SW = stage_words(T);
+    uint32_t *stage = stage_all + warp * SW;
+    if (a.stage && wpl == 8) emit_runs_staged<8>(bm, w0, w1, v0, base, a.out, a.n, stage, SW);
+    else if (a.stage && wpl == 4) emit_runs_staged<4>(bm, w0, w1, v0, base, a.out, a.n, stage, SW);
+    else if (a.stage) emit_words_staged(bm, w0, w1, v0, base, a.out, a.n, stage, SW);
     else if (wpl == 4) emit_words<4>(bm, w0, w1, v0, base, a.out, a.n);
     else if (wpl == 2) emit_words<2>(bm, w0, w1, v0, base, a.out, a.n);
     else emit_words<1>(bm, w0, w1, v0, base, a.out, a.n);
@@ -1133,7 +1134,7 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     // or EMIT_RANK [bitmap | prefix | outputs]
     uint32_t *summ = reinterpret_cast<uint32_t *>(smem);
     uint32_t *stage = summ + kSummaryWords;
-    uint32_t *bm = (!rank && a.stage) ? stage + NW * kStageWords : stage;
+    uint32_t *bm = (!rank && a.stage) ? stage + NW * stage_words(T) : stage;
     uint32_t *pre = bm + w4;
     uint32_t *outs = pre + w4;
     const bool partitioned = a.path == BITSORT_PATH_PARTITION;
@@ -1335,7 +1336,7 @@ template <int T>
 __device__ void item_gscan(const EngineParams &P, const ArrayDesc &a, uint32_t s, char *smem, SharedMisc &m) {
     constexpr int NW = T / 32;
     uint32_t *stage = reinterpret_cast<uint32_t *>(smem) + kSummaryWords;
-    uint32_t *bm = a.stage ? stage + NW * kStageWords : stage;
+    uint32_t *bm = a.stage ? stage + NW * stage_words(T) : stage;
     const uint64_t v0 = (uint64_t)s * a.S;
     const uint64_t vals = min((uint64_t)a.S, a.M - v0);
     const uint32_t words = (uint32_t)((vals + 31) >> 5);

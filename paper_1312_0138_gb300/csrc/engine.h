@@ -128,10 +128,16 @@ struct EngineParams {
 // bitmap word of a slice of up to 2^20 values), used by sparse slices.
 constexpr uint32_t kSummaryWords = 1024;
 constexpr uint32_t kStageWords = 1024 + 4;  // per warp: staged positions (+ room for the 16-byte alignment shift)
+// Staging words per warp for a block of `threads`: the block's staging area
+// stays at 16 x kStageWords words, so a 1024-thread block gives each warp
+// half (a step that does not fit is stored directly).
+__host__ __device__ constexpr uint32_t stage_words(int threads) {
+    return threads > 512 ? 512u + 4u : kStageWords;
+}
 inline uint32_t slice_smem_bytes(uint32_t S, int threads, bool stage) {
     uint32_t words = (S + 31) / 32;
     uint32_t w4 = (words + 3) & ~3u;
-    return kSummaryWords * 4 + w4 * 4 + (stage ? (uint32_t)(threads / 32) * kStageWords * 4 : 0u);
+    return kSummaryWords * 4 + w4 * 4 + (stage ? (uint32_t)(threads / 32) * stage_words(threads) * 4 : 0u);
 }
 // EMIT_RANK: bitmap + per-word prefix + staged outputs
 inline uint32_t rank_smem_bytes(uint32_t S, uint32_t stage_cap) {
