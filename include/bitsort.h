@@ -177,6 +177,24 @@ bitsort_status_t bitsort_multiset_i32(bitsort_ctx_t *ctx, const int32_t *keys, u
                                       int32_t max_value, uint32_t split_bits, int32_t *out,
                                       bitsort_result_t *d_result, bitsort_stream_t stream);
 
+/* bitsort_ex() on keys held in HOST memory: the n keys are copied to device
+ * buffers owned by the context (grown on demand), sorted, and the n output
+ * slots and the outcome copied back, all enqueued on `stream`; the call
+ * returns before they finish (wait on the stream).
+ *   - h_keys, h_out: HOST pointers to n uint32 (page-locked memory lets the
+ *     copies run asynchronously; pageable memory works, but then the copies
+ *     synchronise with the host); h_keys == h_out is allowed.  On DUPLICATE
+ *     or KEY_RANGE, h_out[count..n) is unspecified.
+ *   - h_result: HOST pointer (nullable) that receives the outcome once the
+ *     stream has passed this call.
+ *   - The context's buffers serve every call on it: calls on one context are
+ *     ordered by the stream they are given; to overlap calls (one's copies
+ *     with another's sort), give each stream its own context.
+ *   - Errors as bitsort_ex(); BITSORT_ERR_NOMEM if the device buffers cannot
+ *     be grown. */
+bitsort_status_t bitsort_host(bitsort_ctx_t *ctx, const uint32_t *h_keys, uint64_t n, uint32_t max_value,
+                              uint32_t *h_out, bitsort_result_t *h_result, bitsort_stream_t stream);
+
 /* Wait for `stream`, then return the status of the last sort that wrote its
  * outcome into the context (and its count through `count`, nullable). */
 bitsort_status_t bitsort_sync_status(bitsort_ctx_t *ctx, bitsort_stream_t stream, uint64_t *count);

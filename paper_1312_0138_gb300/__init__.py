@@ -31,7 +31,7 @@ PATH_NAMES = {0: "auto", 1: "fused", 2: "partition", 3: "global"}
 # names every build must export (checked by the CPU test-suite)
 EXPORTS = [
     "bitsort_ctx_create", "bitsort_ctx_destroy", "bitsort_status_string", "bitsort_last_error", "bitsort",
-    "bitsort_ex", "bitsort_i32", "bitsort_multiset", "bitsort_multiset_i32", "bitsort_u16", "bitsort_u8",
+    "bitsort_ex", "bitsort_host", "bitsort_i32", "bitsort_multiset", "bitsort_multiset_i32", "bitsort_u16", "bitsort_u8",
     "bitsort_u64",
     "bitsort_sync_status", "bitsort_batched", "bitsort_batch_plan_create", "bitsort_batch_plan_launch",
     "bitsort_batch_plan_results", "bitsort_batch_plan_device_results", "bitsort_batch_plan_destroy",
@@ -98,6 +98,7 @@ def _declare(lib):
         "bitsort": (st, [p, ctypes.c_size_t, u32, p, p]),
         "bitsort_ex": (st, [p, p, u64, u32, p, p, p]),
         "bitsort_i32": (st, [p, p, u64, ctypes.c_int32, ctypes.c_int32, p, p, p]),
+        "bitsort_host": (st, [p, p, u64, u32, p, p, p]),
         "bitsort_multiset": (st, [p, p, u64, u32, u32, p, p, p]),
         "bitsort_u16": (st, [p, p, u64, ctypes.c_uint16, p, p, p]),
         "bitsort_u8": (st, [p, p, u64, ctypes.c_uint8, p, p, p]),
@@ -178,6 +179,16 @@ def _ptr(t, dtypes=None) -> int:
         raise TypeError(f"keys/out of type {t.dtype}: expected one of {dtypes or (torch.int32, torch.uint32)}")
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _host_ptr(t, allow_int64: bool = False) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("expected a CPU tensor")
+    ok = (torch.int32, torch.uint32) + ((torch.int64,) if allow_int64 else ())
+    if t.dtype not in ok or not t.is_contiguous():
+        raise TypeError(f"host tensor of type {t.dtype}: expected a contiguous tensor of {ok}")
     return t.data_ptr()
 
 
@@ -290,6 +301,17 @@ class Context:
         out = self.multiset_i32_async(keys, min_value, max_value, split_bits, out=out, stream=stream)
         st, cnt = self.sync_status(stream)
         return st, cnt, out
+
+    def sort_host_async(self, h_keys, max_value: int, h_out, h_result=None, stream=None):
+        """Enqueue the sort of HOST keys (CPU int32/uint32 tensor, page-locked
+        for asynchronous copies) into the HOST tensor h_out through the C
+        entry point `bitsort_host`; h_result (CPU int64 tensor of 2) receives
+        (status, count) once the stream passes the call."""
+        _check(load().bitsort_host(self.handle, _host_ptr(h_keys) if h_keys.numel() else None, h_keys.numel(),
+                                   int(max_value), _host_ptr(h_out) if h_out.numel() else None,
+                                   _host_ptr(h_result, allow_int64=True) if h_result is not None else None,
+                                   _stream_handle(stream)), "bitsort_host")
+        return h_out
 
     def sync_status(self, stream=None):
         cnt = ctypes.c_uint64(0)

@@ -128,6 +128,7 @@ extern "C" bitsort_status_t bitsort_ctx_destroy(bitsort_ctx_t *c) {
     if (c->part) cudaFree(c->part);
     if (c->bitmap) cudaFree(c->bitmap);
     if (c->flush) cudaFree(c->flush);
+    if (c->host_io) cudaFree(c->host_io);
     bsx_multiset_free(c);
     bsx_widths_free(c);
     for (int i = 0; i < 9; ++i)
@@ -594,6 +595,40 @@ extern "C" bitsort_status_t bitsort_i32(bitsort_ctx_t *c, const int32_t *keys, u
     const uint64_t M = (uint64_t)span_max + 1;
     bsx_config cfg = bsx_lookup_config(c, n, M);
     return launch_single(c, cfg, k, n, M, o, d_result, s, 0, bias);
+}
+
+extern "C" bitsort_status_t bitsort_host(bitsort_ctx_t *c, const uint32_t *h_keys, uint64_t n, uint32_t max_value,
+                                         uint32_t *h_out, bitsort_result_t *h_result, bitsort_stream_t stream) {
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    if (n > 0 && (!h_keys || !h_out)) return BITSORT_ERR_INVALID;
+    if (n > (uint64_t)max_value + 1) return BITSORT_ERR_INVALID;   // the keys cannot be distinct
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    if (n == 0) {
+        e = cudaMemsetAsync(c->result, 0, sizeof(bitsort_result_t), s);
+    } else {
+        if (c->host_io_cap < n) {
+            c->host_io_cap = 0;
+            e = regrow(c, reinterpret_cast<void **>(&c->host_io), 2 * n * sizeof(uint32_t), s);
+            if (e != cudaSuccess) {
+                c->host_io = nullptr;
+                return BITSORT_ERR_NOMEM;
+            }
+            c->host_io_cap = n;
+        }
+        uint32_t *dk = c->host_io, *dout = c->host_io + c->host_io_cap;
+        e = cudaMemcpyAsync(dk, h_keys, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bsx_check(e);
+        const uint64_t M = (uint64_t)max_value + 1;
+        bitsort_status_t st = launch_single(c, bsx_lookup_config(c, n, M), dk, n, M, dout, nullptr, s, 0);
+        if (st != BITSORT_OK) return st;
+        e = cudaMemcpyAsync(h_out, dout, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess && h_result)
+        e = cudaMemcpyAsync(h_result, c->result, sizeof(bitsort_result_t), cudaMemcpyDeviceToHost, s);
+    return bsx_check(e);
 }
 
 extern "C" bitsort_status_t bitsort(const uint32_t *keys, size_t n, uint32_t max_value, uint32_t *out,

@@ -53,6 +53,8 @@ struct bitsort_ctx {
     void *flush = nullptr;        // L2 flush buffer for tuning
     size_t flush_bytes = 0;
     bool stream_ordered = false;  // used from one stream only: buffers regrow in its order
+    uint32_t *host_io = nullptr;  // bitsort_host(): device copies of the keys and the output (2 x cap)
+    uint64_t host_io_cap = 0;
 
     // multiset path (msort.cu): look-back words tagged with a pass epoch
     // (never cleared between passes) and a small block cleared per call

@@ -276,3 +276,33 @@ def test_sparse_duplicates_and_in_place(ctx):
     keys = gen.floyd(47, 2500, 1 << 22)
     check(ctx, keys, (1 << 22) - 1, path=bs.PATH_PARTITION, S=1 << 20, layout=1, inplace=True)
     check(ctx, gen.floyd(48, 5000, 1 << 20), (1 << 20) - 1, path=bs.PATH_FUSED)   # fused, sparse
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_entry_point(ctx, pinned):
+    """bitsort_host: keys in host memory, output and outcome back in host
+    memory (page-locked or not), equal to the oracle; in place; duplicates."""
+    import torch
+    for n, M in ((100_000, 1 << 20), (300_001, 1 << 28), (0, 16)):
+        keys_np = gen.keys(gen.SEED_BASE + 60 + n, n, M) if n else np.zeros(0, np.uint32)
+        hk = torch.from_numpy(keys_np.view(np.int32).copy())
+        ho = torch.empty(n, dtype=torch.int32)
+        hr = torch.zeros(2, dtype=torch.int64)
+        if pinned:
+            hk, ho, hr = hk.pin_memory(), ho.pin_memory(), hr.pin_memory()
+        s = torch.cuda.Stream()
+        ctx.sort_host_async(hk, M - 1, ho, hr, stream=s)
+        s.synchronize()
+        want_st, want = oracle.bitmap_sort(keys_np, M - 1)
+        assert int(hr[0]) == want_st and int(hr[1]) == want.size
+        assert np.array_equal(ho.numpy().view(np.uint32)[:want.size], want)
+    # in place in host memory, with a repeated key
+    keys_np = gen.keys(gen.SEED_BASE + 61, 50_000, 1 << 24)
+    keys_np[7] = keys_np[3]
+    hk = torch.from_numpy(keys_np.view(np.int32).copy())
+    hr = torch.zeros(2, dtype=torch.int64)
+    ctx.sort_host_async(hk, (1 << 24) - 1, hk, hr)
+    torch.cuda.synchronize()
+    want_st, want = oracle.bitmap_sort(keys_np, (1 << 24) - 1)
+    assert int(hr[0]) == want_st == bs.ERR_DUPLICATE and int(hr[1]) == want.size
+    assert np.array_equal(hk.numpy().view(np.uint32)[:want.size], want)
