@@ -396,6 +396,7 @@ bitsort_status_t multiset_run(bitsort_ctx *c, const uint32_t *keys, uint64_t n, 
     const uint32_t bits = maxv ? 32u - (uint32_t)__builtin_clz(maxv) : 1u;
     uint32_t D = 0, P = 0;
     plan_passes(bits, split_bits, &D, &P);
+    if (P > kMaxPasses || P * (1u << D) > kHistWords) return BITSORT_ERR_INVALID;   // (never: D >= 1, bits <= 32)
     const uint32_t R = 1u << D;
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
     bitsort_status_t st = ensure_multiset_scratch(c, (uint64_t)ntiles * R);
