@@ -1,20 +1,23 @@
-// engine.cu -- the persistent sort kernel for sm_103a.
+// engine.cu -- the sort kernels for sm_103a.
 //
-// One kernel runs every step of the bitmap form of the paper's bitwise sort
-// (Section V, Algorithm 1; result fixed by Theorem 1) for one or many arrays.
-// Work items are taken from a ticket counter in ascending order; see engine.h
-// for the item types.  Design points:
+// The bitmap form of the paper's bitwise sort (Section V, Algorithm 1; result
+// fixed by Theorem 1), split into work items (see engine.h): one persistent
+// kernel runs every item type from a ticket counter in ascending order (one or
+// many arrays), and one phase kernel per item type runs the phases of a single
+// sort as separate launches.  Design points:
 //   * keys stream through 128-bit loads with the streaming cache hint; the
 //     head and tail of a range that is not 16-byte aligned are peeled;
 //   * the bitmap of a bucket lives in shared memory, where the OR of a
-//     shifted one (Table I, Example 2) is a native shared-memory atomic;
-//   * the per-word popcount (Example 6) of a slice is summed per warp, and the
-//     number of set bits before the slice comes from a decoupled look-back
-//     (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled
-//     Look-back", NVIDIA NVR-2016-002) over the slices of the array;
+//     shifted one (Table I, Example 2) is a native shared-memory atomic; a
+//     sparse slice also keeps a summary bitmap of its non-empty words;
+//   * the per-word popcount (Example 6) of a slice is summed per warp; a
+//     partition-path slice starts its outputs at its bucket's known offset,
+//     and only the global-bitmap path chains its slices by a decoupled
+//     look-back (Merrill & Garland, "Single-pass Parallel Prefix Scan with
+//     Decoupled Look-back", NVIDIA NVR-2016-002);
 //   * set-bit positions are written ascending, bit 0 first inside a word
-//     (Section II numbering), staged per warp in shared memory so that every
-//     global store of a warp covers consecutive elements;
+//     (Section II numbering), by neighbouring lanes (coalesced) or staged per
+//     warp in shared memory and written in 16-byte stores (dense words);
 //   * every wait on another CTA is bounded in time (%globaltimer) and in
 //     iterations, and reports a timeout instead of hanging.
 #include <cuda_runtime.h>

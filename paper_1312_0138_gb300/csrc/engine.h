@@ -1,9 +1,11 @@
-// engine.h -- device-side data layout shared by the engine kernel (engine.cu)
-// and the host code that plans and launches it (api.cu, server.cpp).
+// engine.h -- device-side data layout shared by the sort kernels (engine.cu)
+// and the host code that plans and launches them (api.cu, batch.cu,
+// server.cu, noalloc.cu).
 //
 // The sort of one array (the paper's bitwise sort, Section V, in its bit-set
-// form) is split into work items, all executed by one persistent kernel that
-// takes items from a ticket counter in ascending order:
+// form) is split into work items, executed either by one persistent kernel
+// that takes items from a ticket counter in ascending order, or phase by phase
+// by one kernel per item type:
 //
 //   HIST      count the keys of one tile per bucket (bucket = the value range
 //             [b*S, (b+1)*S) of the array's bitmap); the last HIST tile of an
@@ -12,10 +14,11 @@
 //             partition buffer.
 //   BUCKET    build bucket b's bitmap slice in shared memory (OR of shifted
 //             ones, Table I / Example 2), count its set bits (Example 6),
-//             get the number of set bits of all earlier slices by a decoupled
-//             look-back, and write the set-bit positions to the output.  An
-//             array of one bucket is sorted by one BUCKET item straight from
-//             its input (the fused path).
+//             and write the set-bit positions to the output from its
+//             bucket's offset (with distinct keys the set bits of the earlier
+//             buckets are their key counts; repeated keys are closed up by
+//             the array's last CTA).  An array of one bucket is sorted by
+//             one BUCKET item straight from its input (the fused path).
 //   GSCATTER  OR the keys of one tile into a global bitmap (atomics in L2).
 //   GSCAN     load a slice of the global bitmap into shared memory, zero it
 //             behind (so the bitmap is clean for the next call), then count,

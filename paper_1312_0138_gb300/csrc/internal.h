@@ -1,4 +1,4 @@
-// internal.h -- host-side state shared by api.cu, batch.cu and server.cpp.
+// internal.h -- host-side state shared by api.cu, batch.cu, server.cu, noalloc.cu, msort.cu and widths.cu.
 #pragma once
 #include <stdint.h>
 
