@@ -59,11 +59,16 @@ def read_peaks():
 
 
 def engine_source_hash():
-    """Hash of the kernel sources (the device code the counters describe)."""
+    """Hash of the kernel sources (the device code the counters describe),
+    comments and blank space left out so that only code changes count."""
+    import re
     h = hashlib.sha256()
-    for f in ("engine.cu", "engine.h"):
-        with open(os.path.join(ROOT, "paper_1312_0138_gb300", "csrc", f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    for f in ("engine.cu", "engine.h", "ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_1312_0138_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(f.encode() + " ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
