@@ -74,3 +74,62 @@ def test_multiset_full_size(ctx, n, M, kind):
     st, cnt, out = ctx.multiset(to_dev(keys_np), M - 1)
     assert st == bs.OK and cnt == n
     assert np.array_equal(to_host(out), oracle.paper_sort_u32(keys_np))
+
+
+def _check_feistel_output(out_dev, seed, n, M):
+    """Length n, strictly increasing (on the device), and every value v has
+    pi^-1(v) < n for the seeded bijection pi that made the keys: together, the
+    output is the sorted key set."""
+    import torch
+    c = out_dev[:n].to(torch.int64) & 0xFFFFFFFF
+    assert n < 2 or bool((c[1:] > c[:-1]).all())
+    host = to_host(out_dev)[:n]
+    assert n == 0 or int(gen.feistel_inverse(seed, M, host).max()) < n
+
+
+def test_batched_full_size(ctx):
+    """The benchmark's batch (4096 arrays, 2.07 G keys, seeds and sizes as
+    timed) in one persistent launch with the default batch policy: every
+    outcome, every output by its three properties, and a sample of arrays
+    element by element against the oracle."""
+    import torch
+    seed0 = gen.SEED_BASE
+    spec = gen.batch_spec(seed0 + 3, 4096)
+    keys_np = [gen.feistel(seed0 + 7 * i, n, M) for i, (n, M) in enumerate(spec)]
+    keys = [to_dev(k) for k in keys_np]
+    outs = [torch.empty_like(k) for k in keys]
+    plan = ctx.plan([(k, M - 1, o) for k, (n, M), o in zip(keys, spec, outs)])
+    plan.launch()
+    res = plan.results()
+    for i, ((n, M), (st, cnt)) in enumerate(zip(spec, res)):
+        assert st == bs.OK and cnt == n, (i, st, cnt, n)
+        _check_feistel_output(outs[i], seed0 + 7 * i, n, M)
+    for i in range(0, 4096, 97):
+        want_st, want = oracle.bitmap_sort(keys_np[i], spec[i][1] - 1)
+        assert want_st == bs.OK and np.array_equal(to_host(outs[i]), want), i
+    plan.close()
+
+
+def test_served_full_size(ctx):
+    """The benchmark's saturated serving run (300 Poisson requests, n up to
+    2^26, max_value up to 2^32 - 1, 40 GiB budget, 4 streams): every request's
+    outcome and output, and a sample element by element against the oracle."""
+    import torch
+    seed0 = gen.SEED_BASE
+    spec = gen.serve_spec(seed0 + 4, 300, rate_hz=1e6)
+    reqs = []
+    for i, (_, n, M) in enumerate(spec):
+        k = gen.feistel(seed0 + 11 * i, n, M)
+        reqs.append((k, M - 1, to_dev(k)))
+    srv = bs.Server(0, budget_bytes=40 << 30, max_inflight=4)
+    outs = [torch.empty_like(kd) for _, _, kd in reqs]
+    tickets = [srv.submit(kd, mv, o) for (_, mv, kd), o in zip(reqs, outs)]
+    for i, t in enumerate(tickets):
+        st, cnt, _ = srv.wait(t)
+        n, M = spec[i][1], spec[i][2]
+        assert st == bs.OK and cnt == n, (i, st, cnt, n, M)
+        _check_feistel_output(outs[i], seed0 + 11 * i, n, M)
+    srv.close()
+    for i in range(0, 300, 37):
+        want_st, want = oracle.bitmap_sort(reqs[i][0], reqs[i][1])
+        assert want_st == bs.OK and np.array_equal(to_host(outs[i]), want), i
