@@ -261,13 +261,6 @@ __device__ uint64_t lookback(const EngineParams &P, const ArrayDesc &a, uint32_t
 
 // Writes the set-bit positions of bm[w0, w1) in ascending order to
 // out[base ...]: value = v0 + 32*word + bit (Section II numbering, bit 0
-// first).  Each lane takes WPL consecutive words per step; the lanes' counts
-// are prefix-summed across the warp to place them.  STAGE: the positions of
-// a step go through a per-warp shared-memory buffer and leave in coalesced
-// stores; otherwise every lane stores its own positions (consecutive lanes
-// write neighbouring addresses, which stays coalesced at low density).
-// Writes the set-bit positions of bm[w0, w1) in ascending order to
-// out[base ...]: value = v0 + 32*word + bit (Section II numbering, bit 0
 // first).  A warp step covers U groups of 32 consecutive words; lane l holds
 // word l of every group, so neighbouring lanes write neighbouring outputs
 // (coalesced stores), and the U warp-wide prefix sums that place the lanes'
