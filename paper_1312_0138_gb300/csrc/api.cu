@@ -33,7 +33,11 @@ using namespace bsx;
 namespace {
 
 constexpr uint32_t kMaxSliceValues = 1u << 20;   // 128 KiB of bitmap per CTA
-constexpr uint64_t kCapacityScratchMax = 4ull << 30;  // largest CAPACITY partition buffer (bytes)
+// largest CAPACITY partition buffer (bytes): 4 GiB, or twice the keys' own
+// bytes for a larger array (a dense array of 2^31 keys over 2^32 values
+// then skips the histogram pass for 16 GiB of scratch)
+constexpr uint64_t kCapacityScratchMax = 4ull << 30;
+inline uint64_t capacity_scratch_max(uint64_t n) { return n * 8 > kCapacityScratchMax ? n * 8 : kCapacityScratchMax; }
 constexpr uint64_t kDefaultWaitNs = 4000ull * 1000ull * 1000ull;
 
 inline uint32_t round_up_u32(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
@@ -247,7 +251,7 @@ bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
     if (cfg.path == BITSORT_PATH_PARTITION && cfg.layout == LAYOUT_CAPACITY) {
         const uint64_t nb = ceil_div(M, cfg.S);
         const uint64_t cap = std::min<uint64_t>(cfg.S, n);
-        if (nb * cap * 4 > kCapacityScratchMax) cfg.layout = LAYOUT_EXACT;
+        if (nb * cap * 4 > capacity_scratch_max(n)) cfg.layout = LAYOUT_EXACT;
     }
     if (cfg.path == BITSORT_PATH_GLOBAL) cfg.emit = EMIT_WORD;   // a global slice has no keys to rank
     if (cfg.emit != EMIT_WORD && cfg.emit != EMIT_RANK) cfg.emit = EMIT_WORD;
@@ -415,12 +419,23 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     memset(&p, 0, sizeof(p));
     ArrayDesc &a = p.one;
     bsx_describe(cfg, keys, out, n, M, a);
-    a.stall = stall;
-    a.bias = bias;
     bool alias = keys == out;
     if (cfg.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
-        bitsort_status_t st = bsx_ensure_part(c, (uint64_t)a.nslices * a.cap, stream);
+        const uint64_t entries = (uint64_t)a.nslices * a.cap;
+        bitsort_status_t st = bsx_ensure_part(c, entries, stream);
+        if (st == BITSORT_ERR_NOMEM && entries * 4 > kCapacityScratchMax) {
+            // no room for a large capacity buffer: the exact layout needs
+            // none outside the output (the failed allocation is not sticky)
+            cudaGetLastError();
+            cfg.layout = LAYOUT_EXACT;
+            bsx_describe(cfg, keys, out, n, M, a);
+            st = BITSORT_OK;
+        }
         if (st != BITSORT_OK) return st;
+    }
+    a.stall = stall;
+    a.bias = bias;
+    if (cfg.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
         a.part = c->part;
     } else if (cfg.path == BITSORT_PATH_PARTITION) {
         if (alias) {

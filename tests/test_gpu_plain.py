@@ -109,6 +109,20 @@ def test_default_plan_n100k_range_2e20(ctx):
     check(ctx, keys, (1 << 20) - 1)
 
 
+def test_default_layout_by_scratch():
+    # the capacity layout's buffer (about 4 bytes per value of the range) is
+    # allowed up to 4 GiB, or up to twice the keys' own bytes: dense 2^31
+    # keys over 2^32 values use it, sparse 2^24 keys over 2^32 values take
+    # the exact layout (no buffer beyond the output)
+    c = bs.Context(0)
+    try:
+        assert c.get_config(1 << 31, (1 << 32) - 1)["layout"] == "capacity"
+        assert c.get_config(1 << 24, (1 << 32) - 1)["layout"] == "exact"
+        assert c.get_config(1 << 24, (1 << 28) - 1)["layout"] == "capacity"
+    finally:
+        c.close()
+
+
 def test_full_permutation_closed_form(ctx):
     for M in (32, 1000, 1 << 16, (1 << 20) + 5):
         keys = gen.feistel(M, M, M)
