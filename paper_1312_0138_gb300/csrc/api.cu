@@ -495,10 +495,11 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     // staging, or one or two slices per SM, 512 threads stay faster.
     int Tp = T, Tb = T;
     if (T == 512 && a.path == BITSORT_PATH_PARTITION) {
-        const bool bulk_part = ((uintptr_t)keys & 15u) == 0 && cfg.stream_part;   // streaming partition stays
-        if (a.nslices >= 1024 && !bulk_part &&
-            part_smem_bytes(a.nslices, (uint32_t)(kKeysPerThread * 1024)) <= c->smem_optin)
-            Tp = 1024;
+        const bool bulk_part = ((uintptr_t)keys & 15u) == 0 && cfg.stream_part;
+        const uint32_t wide = (uint32_t)(kKeysPerThread * 1024);
+        const uint32_t part_smem =
+            bulk_part ? part_stream_smem_bytes(a.nslices, wide) : part_smem_bytes(a.nslices, wide);
+        if (a.nslices >= 1024 && part_smem <= c->smem_optin) Tp = 1024;
         if (!cfg.stage && cfg.emit == EMIT_WORD && a.nslices >= 4u * (uint32_t)c->sms &&
             slice_smem_bytes(cfg.S, 1024, false) <= c->smem_optin)
             Tb = 1024;

@@ -49,6 +49,9 @@ CONFIGS = [
     ("cap_S1M_runs8", bs.PATH_PARTITION, 1 << 20, 512, dict(layout=1, stage=1, words_per_lane=8)),
     ("cap_stream_S64K", bs.PATH_PARTITION, 1 << 16, 512, dict(layout=1, part_stream=1)),
     ("exact_stream_odd_256", bs.PATH_PARTITION, 300_032, 256, dict(layout=0, part_stream=1)),
+    # 1024 or more buckets: the streaming partition runs at 1024 threads (16 Ki-key tiles)
+    ("cap_stream_S4096_wide", bs.PATH_PARTITION, 4096, 512, dict(layout=1, part_stream=1)),
+    ("exact_stream_S16K_wide", bs.PATH_PARTITION, 16384, 512, dict(layout=0, part_stream=1)),
     ("exact_odd_runs4_256", bs.PATH_PARTITION, 300_032, 256, dict(layout=0, stage=1, words_per_lane=4)),
     ("cap_S4096_runs8_persist", bs.PATH_PARTITION, 4096, 512, dict(layout=1, stage=1, words_per_lane=8,
                                                                     persistent=1)),
@@ -91,6 +94,15 @@ STRATS = [
     ("runs8", dict(path=bs.PATH_PARTITION, S=4096, layout=1, stage=1, words_per_lane=8)),
     ("stream", dict(path=bs.PATH_PARTITION, S=4096, layout=1, part_stream=1)),
 ]
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_stream_partition_many_tiles_per_cta(ctx, layout):
+    # 4096 buckets: the streaming partition runs at 1024 threads, one CTA per
+    # SM, so each CTA takes several 16 Ki-key tiles through both landing
+    # buffers; the odd n leaves a ragged last tile loaded by the threads
+    keys = gen.floyd(gen.SEED_BASE + 77, 8_000_009, 1 << 24)
+    check(ctx, keys, (1 << 24) - 1, path=bs.PATH_PARTITION, S=4096, threads=512, layout=layout, part_stream=1)
 
 
 @pytest.mark.parametrize("layout", [0, 1])
