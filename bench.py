@@ -298,37 +298,45 @@ def run_plain(args, w, ws, rank, local):
 
     # end to end through the host-buffer entry point (bitsort_host): every
     # step copies its keys from pinned host memory, sorts, and copies the
-    # output and the outcome back.  Consecutive steps alternate between two
-    # streams, each with its own context, so that one step's copies overlap
-    # the other's sort and copies (the copy engines work in both directions).
+    # output and the outcome back.  Consecutive steps rotate over three
+    # streams, each with its own context: a stream runs its step's copy in,
+    # sort and copy out one after the other, so with three of them in flight
+    # the copies of one step overlap the sort and the copies of the others
+    # (the copy engines work in both directions at once).
     e2e_steps = max(3, min(args.steps, args.e2e_steps))
     hkeys = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
+    nl = 3
     lanes = []
-    for li in range(2):
+    for li in range(nl):
         lanes.append(dict(ctx=ctx if li == 0 else bs.Context(local), stream=stream if li == 0 else torch.cuda.Stream(),
                           hout=torch.empty(n, dtype=torch.int32).pin_memory(),
                           hres=torch.zeros(2, dtype=torch.int64).pin_memory()))
-    for i in range(4):
-        ln = lanes[i % 2]
+    for i in range(2 * nl):
+        ln = lanes[i % nl]
         ln["ctx"].sort_host_async(hkeys, M - 1, ln["hout"], ln["hres"], stream=ln["stream"])
     torch.cuda.synchronize()
     barrier(ws)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    lanes[1]["stream"].wait_event(e0)
+    for ln in lanes[1:]:
+        ln["stream"].wait_event(e0)
     for i in range(e2e_steps):
-        ln = lanes[i % 2]
+        ln = lanes[i % nl]
         ln["ctx"].sort_host_async(hkeys, M - 1, ln["hout"], ln["hres"], stream=ln["stream"])
-    done1 = torch.cuda.Event()
-    done1.record(lanes[1]["stream"])
-    stream.wait_event(done1)
+    for ln in lanes[1:]:
+        done = torch.cuda.Event()
+        done.record(ln["stream"])
+        stream.wait_event(done)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1) / e2e_steps)
     for ln in lanes:
         assert int(ln["hres"][0]) & 0xFFFFFFFF == bs.OK and int(ln["hres"][1]) == n
         assert bool(np.all(np.diff(ln["hout"].numpy().view(np.uint32)[:1 << 20].astype(np.int64)) > 0))
-    lanes[1]["ctx"].close()
+    for ln in lanes[1:]:
+        ln["ctx"].close()
+    link = time_host_link(hkeys, lanes[0]["hout"], out, stream)
+    link["e2e_gbs"] = (8 * n + 16) / (e2e_ms * 1e-3) / 1e9   # bytes each rank moves per step / step time
 
     comparison = None
     if not args.no_cub:
@@ -360,13 +368,59 @@ def run_plain(args, w, ws, rank, local):
                              f"peak = {peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)"},
         "e2e": {"value": job_gkeys_s(ws, n, e2e_ms), "unit": "Gkeys/s", "h2d_bytes_per_step": 4 * n,
                 "d2h_bytes_per_step": 4 * n + 16, "api": "bitsort_host (pinned host buffers)",
-                "overlap": "two streams with a context each; consecutive steps overlap"},
+                "overlap": "three streams with a context each; consecutive steps overlap",
+                "link": link},
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
         "comparison": comparison,
     }
     print(json.dumps(line), flush=True)
+
+
+def time_host_link(hbuf, hout, dbuf, stream, reps=10):
+    """Host<->device copy rates of this GPU for one step's buffers (pinned
+    host memory, copy engines): host-to-device alone, device-to-host alone,
+    and both at once on two streams, which is what overlapped steps of the
+    end-to-end loop need.  For large arrays the end-to-end loop is bound by
+    the both-at-once rate."""
+    import torch
+    dtmp = torch.empty_like(dbuf)
+    other = torch.cuda.Stream()
+    nbytes = hbuf.numel() * hbuf.element_size()
+
+    def timed(fn):
+        ms = []
+        for i in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            other.wait_event(e0)
+            fn()
+            done = torch.cuda.Event()
+            done.record(other)
+            stream.wait_event(done)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    def h2d(s):
+        with torch.cuda.stream(s):
+            dtmp.copy_(hbuf, non_blocking=True)
+
+    def d2h(s):
+        with torch.cuda.stream(s):
+            hout.copy_(dbuf, non_blocking=True)
+
+    t_h2d = timed(lambda: h2d(stream))
+    t_d2h = timed(lambda: d2h(stream))
+    t_both = timed(lambda: (h2d(stream), d2h(other)))
+    return {"h2d_gbs": nbytes / (t_h2d * 1e-3) / 1e9, "d2h_gbs": nbytes / (t_d2h * 1e-3) / 1e9,
+            "duplex_gbs": 2 * nbytes / (t_both * 1e-3) / 1e9,
+            "note": "h2d/d2h/duplex: one copy of a step's keys in, out, and both at once (pinned host "
+                    "buffers, copy engines, a lone step: latency-bound for small arrays); e2e_gbs: the "
+                    "bytes the end-to-end loop moves per step over its step time"}
 
 
 class L2Flush:
