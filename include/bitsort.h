@@ -377,6 +377,27 @@ bitsort_status_t bitsort_set_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max
 /* The configuration the context would use for (n, max_value). */
 bitsort_status_t bitsort_get_config(bitsort_ctx_t *ctx, uint64_t n, uint32_t max_value, bitsort_config_t *config);
 
+/* Shape of a plan (bitsort_plan_rule). */
+typedef struct {
+    uint32_t slices;          /* bitmap slices (buckets, or scan slices of the global bitmap; 1 when fused) */
+    uint32_t tile_keys;       /* keys per partition / scatter tile */
+    uint32_t part_threads;    /* block size of the histogram and partition phases */
+    uint32_t bucket_threads;  /* block size of the bucket phase */
+    uint32_t smem_bytes;      /* largest dynamic shared memory a launch of the plan asks for, per block */
+    uint32_t reserved;
+    uint64_t scratch_bytes;   /* partition buffer of the capacity layout (0 for the other layouts) */
+} bitsort_plan_shape_t;
+
+/* The built-in plan rule for an array of n distinct keys bounded by
+ * max_value, out of place, keys 16-byte aligned, on a device with `sms`
+ * streaming multiprocessors and `smem_per_block` bytes of opt-in shared
+ * memory per block: the plan a context uses when its table holds no tuned
+ * entry for the size class.  Host logic only: needs no GPU and no context,
+ * launches nothing.  *shape is nullable.  INVALID: sms < 1,
+ * smem_per_block == 0, config NULL, or n > max_value + 1. */
+bitsort_status_t bitsort_plan_rule(int sms, uint32_t smem_per_block, uint64_t n, uint32_t max_value,
+                                   bitsort_config_t *config, bitsort_plan_shape_t *shape);
+
 /* Batch policy of a context (used by plans created afterwards).  Arrays whose
  * values fit one slice (max_value + 1 <= slice_values) are each sorted by one
  * fused shared-memory slice; the others take `path` (BITSORT_PATH_PARTITION:

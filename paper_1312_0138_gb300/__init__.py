@@ -39,7 +39,7 @@ EXPORTS = [
     "bitsort_server_destroy", "bitsort_autotune", "bitsort_set_config", "bitsort_get_config",
     "bitsort_tune_save", "bitsort_tune_load", "bitsort_set_wait_limit_ms", "bitsort_debug_stalled_launch",
     "bitsort_kernel_launches", "bitsort_noalloc", "bitsort_set_phase_timing", "bitsort_phase_times",
-    "bitsort_set_batch_config", "bitsort_get_batch_config", "bitsort_batch_autotune",
+    "bitsort_set_batch_config", "bitsort_get_batch_config", "bitsort_batch_autotune", "bitsort_plan_rule",
 ]
 
 
@@ -51,6 +51,15 @@ class BitsortError(RuntimeError):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("count", ctypes.c_uint64)]
+
+
+class PlanShape(ctypes.Structure):
+    _fields_ = [("slices", ctypes.c_uint32), ("tile_keys", ctypes.c_uint32), ("part_threads", ctypes.c_uint32),
+                ("bucket_threads", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("scratch_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class Config(ctypes.Structure):
@@ -120,6 +129,7 @@ def _declare(lib):
         "bitsort_autotune": (st, [p, p, p, u64, u32, ctypes.POINTER(Config)]),
         "bitsort_set_config": (st, [p, u64, u32, ctypes.POINTER(Config)]),
         "bitsort_get_config": (st, [p, u64, u32, ctypes.POINTER(Config)]),
+        "bitsort_plan_rule": (st, [i32, u32, u64, u32, ctypes.POINTER(Config), ctypes.POINTER(PlanShape)]),
         "bitsort_tune_save": (st, [p, ctypes.c_char_p]),
         "bitsort_tune_load": (st, [p, ctypes.c_char_p]),
         "bitsort_set_wait_limit_ms": (st, [p, u32]),
@@ -537,3 +547,14 @@ def sync_status(stream=None):
     cnt = ctypes.c_uint64(0)
     st = load().bitsort_sync_status(None, _stream_handle(stream), ctypes.byref(cnt))
     return st, cnt.value
+
+
+def plan_rule(sms: int, smem_per_block: int, n: int, max_value: int):
+    """The built-in plan for n distinct keys bounded by max_value on a device
+    with `sms` SMs and `smem_per_block` bytes of opt-in shared memory per
+    block, through the C entry point `bitsort_plan_rule` (host logic only: no
+    GPU needed).  Returns (configuration dict, shape dict)."""
+    cfg, shape = Config(), PlanShape()
+    _check(load().bitsort_plan_rule(int(sms), int(smem_per_block), int(n), int(max_value), ctypes.byref(cfg),
+                                    ctypes.byref(shape)), "bitsort_plan_rule")
+    return cfg.as_dict(), shape.as_dict()

@@ -177,7 +177,7 @@ uint64_t bsx_div_magic(uint32_t S) {
     return UINT64_MAX / S + 1;
 }
 
-bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M) {
+bsx_config bsx_default_config(int sms, uint64_t n, uint64_t M) {
     bsx_config cfg;
     cfg.threads = 256;
     cfg.wpl = 2;
@@ -211,7 +211,7 @@ bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M) {
     cfg.wpl = 1;
     cfg.emit = EMIT_WORD;
     cfg.stage = n * 10 >= M;
-    uint64_t target = 2ull * (uint64_t)c->sms;
+    uint64_t target = 2ull * (uint64_t)sms;
     uint64_t S = ceil_div(M, target);
     uint64_t lo = std::max<uint64_t>(4096, ceil_div(M, kMaxSlices));
     S = std::max(S, lo);
@@ -224,7 +224,7 @@ bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M) {
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->table.find(std::make_pair(ilog2_ceil(n), ilog2_ceil(M)));
     if (it != c->table.end()) return it->second;
-    return bsx_default_config(c, n, M);
+    return bsx_default_config(c->sms, n, M);
 }
 
 // Make a configuration valid for (n, M): the slice count within bounds, the
@@ -395,11 +395,11 @@ uint32_t bsx_single_segments(const ArrayDesc &a, Segment *seg, uint32_t *nseg) {
 
 // Shrink a configuration until its shared memory fits one CTA: rank
 // emission falls back to word emission, staging to direct stores.
-static bsx_config fit_smem(const bitsort_ctx *c, bsx_config cfg, uint64_t n, uint64_t M) {
+static bsx_config fit_smem(uint32_t smem_optin, bsx_config cfg, uint64_t n, uint64_t M) {
     for (int tries = 0; tries < 3; ++tries) {
         ArrayDesc probe;
         bsx_describe(cfg, nullptr, nullptr, n, M, probe);
-        if (bsx_smem_for(cfg, probe.nslices, probe.tile_keys, probe.stage_cap) <= c->smem_optin) break;
+        if (bsx_smem_for(cfg, probe.nslices, probe.tile_keys, probe.stage_cap) <= smem_optin) break;
         if (cfg.emit == EMIT_RANK) cfg.emit = EMIT_WORD;
         else if (cfg.stage) cfg.stage = false;
         else break;
@@ -407,32 +407,82 @@ static bsx_config fit_smem(const bitsort_ctx *c, bsx_config cfg, uint64_t n, uin
     return cfg;
 }
 
+// The plan of one array on a device with `sms` SMs and `smem_optin` bytes of
+// shared memory per block (host logic only): the configuration after the
+// size rules and the shared-memory fit, the array's descriptor (pointers
+// left null), the block size of each phase and each phase's shared memory.
+// In place, a capacity bucket that overflowed (repeated keys) would read the
+// whole input while other slices write their outputs over it: exact bucket
+// ranges never overflow, so an in-place sort takes the exact layout.
+// A phased 512-thread plan runs two phases at 1024 threads (one CTA per SM)
+// where that measured faster on GB300: the partition with a wide fan-out
+// (its tile doubles to 16 Ki keys, so the per-bucket work of a tile is
+// spread over twice the keys: 16.0 -> 12.6 ms at 4096 buckets, n = 2^31),
+// and the bucket phase when every SM works through many slices without
+// staging (255.9 -> 212.0 us for 4096 sparse slices, n = 2^24); with
+// staging, or one or two slices per SM, 512 threads stay faster.
+void bsx_plan_single(int sms, uint32_t smem_optin, const bsx_config &cfg0, uint64_t n, uint64_t M, bool in_place,
+                     bool keys_aligned, bsx_single_plan &pl) {
+    bsx_config cfg = fit_smem(smem_optin, bsx_sanitize(cfg0, n, M), n, M);
+    if (in_place && cfg.path == BITSORT_PATH_PARTITION && cfg.layout == LAYOUT_CAPACITY) cfg.layout = LAYOUT_EXACT;
+    ArrayDesc &a = pl.a;
+    bsx_describe(cfg, nullptr, nullptr, n, M, a);
+    const int T = cfg.threads;
+    const bool partitioned = a.path == BITSORT_PATH_PARTITION;
+    pl.stream_part = !cfg.persistent && partitioned && keys_aligned && cfg.stream_part;
+    int Tp = T, Tb = T;
+    if (!cfg.persistent && T == 512 && partitioned) {
+        const uint32_t wide = (uint32_t)(kKeysPerThread * 1024);
+        const uint32_t part_smem =
+            pl.stream_part ? part_stream_smem_bytes(a.nslices, wide) : part_smem_bytes(a.nslices, wide);
+        if (a.nslices >= 1024 && part_smem <= smem_optin) Tp = 1024;
+        if (!cfg.stage && cfg.emit == EMIT_WORD && a.nslices >= 4u * (uint32_t)sms &&
+            slice_smem_bytes(cfg.S, 1024, false) <= smem_optin)
+            Tb = 1024;
+    }
+    if (Tp != T) {
+        a.tile_keys = (uint32_t)(kKeysPerThread * Tp);
+        a.key_tiles = (uint32_t)ceil_div(n, (uint64_t)a.tile_keys);
+    }
+    pl.cfg = cfg;
+    pl.Tp = Tp;
+    pl.Tb = Tb;
+    pl.slice_smem = cfg.emit == EMIT_RANK ? rank_smem_bytes(cfg.S, a.stage_cap) : slice_smem_bytes(cfg.S, Tb, cfg.stage);
+    pl.part_smem = !partitioned ? 0u
+                   : pl.stream_part ? part_stream_smem_bytes(a.nslices, a.tile_keys)
+                                    : part_smem_bytes(a.nslices, a.tile_keys);
+    pl.hist_smem = partitioned && a.layout == LAYOUT_EXACT ? hist_smem_bytes(a.nslices) : 0u;
+    pl.engine_smem = cfg.persistent ? bsx_smem_for(cfg, a.nslices, a.tile_keys, a.stage_cap) : 0u;
+}
+
 static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, const uint32_t *keys, uint64_t n,
                                       uint64_t M, uint32_t *out, bitsort_result_t *d_result, cudaStream_t stream,
                                       uint32_t stall, uint32_t bias = 0) {
-    bsx_config cfg = fit_smem(c, bsx_sanitize(cfg0, n, M), n, M);
-    // in place, a capacity bucket that overflowed (repeated keys) would read
-    // the whole input while other slices write their outputs over it: exact
-    // bucket ranges never overflow
-    if (keys == out && cfg.path == BITSORT_PATH_PARTITION && cfg.layout == LAYOUT_CAPACITY) cfg.layout = LAYOUT_EXACT;
-    EngineParams p;
-    memset(&p, 0, sizeof(p));
-    ArrayDesc &a = p.one;
-    bsx_describe(cfg, keys, out, n, M, a);
-    bool alias = keys == out;
-    if (cfg.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
-        const uint64_t entries = (uint64_t)a.nslices * a.cap;
+    const bool alias = keys == out;
+    const bool aligned = ((uintptr_t)keys & 15u) == 0;
+    bsx_single_plan pl;
+    bsx_plan_single(c->sms, c->smem_optin, cfg0, n, M, alias, aligned, pl);
+    if (pl.cfg.path == BITSORT_PATH_PARTITION && pl.a.layout == LAYOUT_CAPACITY) {
+        const uint64_t entries = (uint64_t)pl.a.nslices * pl.a.cap;
         bitsort_status_t st = bsx_ensure_part(c, entries, stream);
         if (st == BITSORT_ERR_NOMEM && entries * 4 > kCapacityScratchMax) {
             // no room for a large capacity buffer: the exact layout needs
             // none outside the output (the failed allocation is not sticky)
             cudaGetLastError();
-            cfg.layout = LAYOUT_EXACT;
-            bsx_describe(cfg, keys, out, n, M, a);
+            bsx_config exact = pl.cfg;
+            exact.layout = LAYOUT_EXACT;
+            bsx_plan_single(c->sms, c->smem_optin, exact, n, M, alias, aligned, pl);
             st = BITSORT_OK;
         }
         if (st != BITSORT_OK) return st;
     }
+    const bsx_config &cfg = pl.cfg;
+    EngineParams p;
+    memset(&p, 0, sizeof(p));
+    p.one = pl.a;
+    ArrayDesc &a = p.one;
+    a.keys = keys;
+    a.out = out;
     a.stall = stall;
     a.bias = bias;
     if (cfg.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
@@ -465,7 +515,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     const int T = cfg.threads;
     if (cfg.persistent) {
         // every phase in one persistent launch (items in ticket order)
-        uint32_t smem = bsx_smem_for(cfg, a.nslices, a.tile_keys, a.stage_cap);
+        const uint32_t smem = pl.engine_smem;
         if (smem > c->smem_optin) return BITSORT_ERR_INVALID;
         int grid = bsx_grid_for(c, T, smem, p.total_items);
         if (c->timing) {
@@ -484,30 +534,10 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         c->launches.fetch_add(1);
         return BITSORT_OK;
     }
-    // one kernel per phase, each at the occupancy its shared memory allows;
-    // later phases use programmatic dependent launch to hide the launch gap.
-    // A 512-thread plan runs two phases at 1024 threads (one CTA per SM)
-    // where that measured faster on GB300: the partition with a wide fan-out
-    // (its tile doubles to 16 Ki keys, so the per-bucket work of a tile is
-    // spread over twice the keys: 16.0 -> 12.6 ms at 4096 buckets, n = 2^31),
-    // and the bucket phase when every SM works through many slices without
-    // staging (255.9 -> 212.0 us for 4096 sparse slices, n = 2^24); with
-    // staging, or one or two slices per SM, 512 threads stay faster.
-    int Tp = T, Tb = T;
-    if (T == 512 && a.path == BITSORT_PATH_PARTITION) {
-        const bool bulk_part = ((uintptr_t)keys & 15u) == 0 && cfg.stream_part;
-        const uint32_t wide = (uint32_t)(kKeysPerThread * 1024);
-        const uint32_t part_smem =
-            bulk_part ? part_stream_smem_bytes(a.nslices, wide) : part_smem_bytes(a.nslices, wide);
-        if (a.nslices >= 1024 && part_smem <= c->smem_optin) Tp = 1024;
-        if (!cfg.stage && cfg.emit == EMIT_WORD && a.nslices >= 4u * (uint32_t)c->sms &&
-            slice_smem_bytes(cfg.S, 1024, false) <= c->smem_optin)
-            Tb = 1024;
-    }
-    if (Tp != T) {
-        a.tile_keys = (uint32_t)(kKeysPerThread * Tp);
-        a.key_tiles = (uint32_t)ceil_div(n, (uint64_t)a.tile_keys);
-    }
+    // one kernel per phase, each at the occupancy its shared memory allows
+    // and with the plan's block size; later phases use programmatic
+    // dependent launch to hide the launch gap
+    const int Tp = pl.Tp, Tb = pl.Tb;
     int launched = 0;
     auto phase = [&](int kind, uint32_t items, uint32_t smem) -> bool {
         const int Tk = (kind == IT_HIST || kind == IT_PART || kind == IT_PARTS) ? Tp : kind == IT_BUCKET ? Tb : T;
@@ -541,19 +571,15 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         }
         return true;
     };
-    const uint32_t sl = cfg.emit == EMIT_RANK ? rank_smem_bytes(cfg.S, a.stage_cap)
-                                              : slice_smem_bytes(cfg.S, Tb, cfg.stage);
+    const uint32_t sl = pl.slice_smem;
     bool ok = true;
     if (a.path == BITSORT_PATH_FUSED) {
         ok = phase(IT_BUCKET, 1, sl);
     } else if (a.path == BITSORT_PATH_PARTITION) {
-        // tiles of 16-byte aligned keys stream through bulk copies
-        const bool stream = ((uintptr_t)keys & 15u) == 0 && cfg.stream_part;
-        const int pk = stream ? (int)IT_PARTS : (int)IT_PART;
-        const uint32_t ps = stream ? part_stream_smem_bytes(a.nslices, a.tile_keys)
-                                   : part_smem_bytes(a.nslices, a.tile_keys);
-        if (a.layout == LAYOUT_EXACT) ok = phase(IT_HIST, a.key_tiles, hist_smem_bytes(a.nslices));
-        ok = ok && phase(pk, a.key_tiles, ps) && phase(IT_BUCKET, a.nslices, sl);
+        // tiles of 16-byte aligned keys may stream through bulk copies
+        const int pk = pl.stream_part ? (int)IT_PARTS : (int)IT_PART;
+        if (a.layout == LAYOUT_EXACT) ok = phase(IT_HIST, a.key_tiles, pl.hist_smem);
+        ok = ok && phase(pk, a.key_tiles, pl.part_smem) && phase(IT_BUCKET, a.nslices, sl);
     } else {
         ok = phase(IT_GSCATTER, a.key_tiles, 0) && phase(IT_GSCAN, a.nslices, sl);
     }
@@ -756,7 +782,7 @@ extern "C" bitsort_status_t bitsort_set_config(bitsort_ctx_t *c, uint64_t n, uin
         return BITSORT_OK;
     }
     if (in->path < BITSORT_PATH_FUSED || in->path > BITSORT_PATH_GLOBAL) return BITSORT_ERR_INVALID;
-    bsx_config cfg = bsx_default_config(c, n, M);
+    bsx_config cfg = bsx_default_config(c->sms, n, M);
     cfg.path = (bitsort_path_t)in->path;
     if (in->slice_values) cfg.S = in->slice_values;
     if (in->block_threads) cfg.threads = (int)in->block_threads;
@@ -777,6 +803,27 @@ extern "C" bitsort_status_t bitsort_get_config(bitsort_ctx_t *c, uint64_t n, uin
     if (!c || !out) return BITSORT_ERR_INVALID;
     uint64_t M = (uint64_t)max_value + 1;
     to_public(bsx_sanitize(bsx_lookup_config(c, n, M), n, M), out);
+    return BITSORT_OK;
+}
+
+extern "C" bitsort_status_t bitsort_plan_rule(int sms, uint32_t smem_per_block, uint64_t n, uint32_t max_value,
+                                              bitsort_config_t *config, bitsort_plan_shape_t *shape) {
+    if (sms < 1 || smem_per_block == 0 || !config) return BITSORT_ERR_INVALID;
+    const uint64_t M = (uint64_t)max_value + 1;
+    if (n > M) return BITSORT_ERR_INVALID;
+    bsx_single_plan pl;
+    bsx_plan_single(sms, smem_per_block, bsx_default_config(sms, n, M), n, M, false, true, pl);
+    to_public(pl.cfg, config);
+    if (shape) {
+        memset(shape, 0, sizeof(*shape));
+        shape->slices = pl.a.nslices;
+        shape->tile_keys = pl.a.tile_keys;
+        shape->part_threads = (uint32_t)pl.Tp;
+        shape->bucket_threads = (uint32_t)pl.Tb;
+        shape->smem_bytes = pl.cfg.persistent ? pl.engine_smem
+                                              : std::max(pl.slice_smem, std::max(pl.part_smem, pl.hist_smem));
+        shape->scratch_bytes = pl.a.layout == LAYOUT_CAPACITY ? (uint64_t)pl.a.nslices * pl.a.cap * 4u : 0u;
+    }
     return BITSORT_OK;
 }
 
@@ -826,7 +873,7 @@ std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_
         }
         if (M <= kMaxSliceValues) push(BITSORT_PATH_FUSED, M, threads, 1, true, LAYOUT_EXACT);
         for (int k : {1, 2, 3}) {   // partition tiles streamed through bulk copies
-            bsx_config sc = bsx_sanitize(bsx_default_config(c, n, M), n, M);
+            bsx_config sc = bsx_sanitize(bsx_default_config(c->sms, n, M), n, M);
             sc.threads = threads;
             sc.S = (uint32_t)ceil_div(M, (uint64_t)k * c->sms);
             sc.stream_part = true;
@@ -834,7 +881,7 @@ std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_
             if (sc.path == BITSORT_PATH_PARTITION) out.push_back(sc);
         }
         for (int k : {2, 4}) {
-            bsx_config pc = bsx_sanitize(bsx_default_config(c, n, M), n, M);
+            bsx_config pc = bsx_sanitize(bsx_default_config(c->sms, n, M), n, M);
             pc.threads = threads;
             pc.S = (uint32_t)ceil_div(M, (uint64_t)k * c->sms);
             pc.persistent = true;
@@ -879,7 +926,7 @@ extern "C" bitsort_status_t bitsort_autotune(bitsort_ctx_t *c, const uint32_t *k
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     double best = 1e30;
-    bsx_config best_cfg = bsx_default_config(c, n, M);
+    bsx_config best_cfg = bsx_default_config(c->sms, n, M);
     for (const bsx_config &cfg : bsx_candidates(c, n, M)) {
         // one warm-up, then the median of five cold-L2 runs
         ArrayDesc probe;

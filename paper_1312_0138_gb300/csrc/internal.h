@@ -98,13 +98,24 @@ bitsort_status_t bsx_check(cudaError_t e);
 void bsx_note_error(int e, const char *where);
 bitsort_ctx *bsx_default_ctx();
 uint64_t bsx_div_magic(uint32_t S);
-bsx_config bsx_default_config(const bitsort_ctx *c, uint64_t n, uint64_t M);
+bsx_config bsx_default_config(int sms, uint64_t n, uint64_t M);
 bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M);
 bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M);
 uint32_t bsx_smem_for(const bsx_config &cfg, uint32_t nslices, uint32_t tile_keys, uint32_t stage_cap);
 uint32_t bsx_stage_cap(const bsx_config &cfg, uint64_t n, uint64_t M);
 void bsx_describe(const bsx_config &cfg, const uint32_t *keys, uint32_t *out, uint64_t n, uint64_t M,
                   bsx::ArrayDesc &a);
+// plan of one array (api.cu, bsx_plan_single): host logic only
+struct bsx_single_plan {
+    bsx_config cfg;
+    bsx::ArrayDesc a;                 // descriptor shape; pointers null
+    int Tp = 0, Tb = 0;               // block size of the HIST/PART phases and of the BUCKET phase
+    bool stream_part = false;         // the partition streams its tiles through bulk copies
+    uint32_t slice_smem = 0, part_smem = 0, hist_smem = 0;   // dynamic shared memory per phase (bytes)
+    uint32_t engine_smem = 0;         // persistent plan: of the one launch
+};
+void bsx_plan_single(int sms, uint32_t smem_optin, const bsx_config &cfg0, uint64_t n, uint64_t M, bool in_place,
+                     bool keys_aligned, bsx_single_plan &pl);
 bool bsx_ranges_overlap(const void *a, const void *b, uint64_t bytes);
 int bsx_grid_for(bitsort_ctx *c, int threads, uint32_t smem, uint32_t items);
 bitsort_status_t bsx_validate(const uint32_t *keys, uint64_t n, uint32_t max_value, const uint32_t *out);
