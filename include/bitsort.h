@@ -79,7 +79,17 @@ typedef struct bitsort_ctx bitsort_ctx_t;
 
 /* Create a context on CUDA device `device` (made current by the call).
  * Returns BITSORT_ERR_INVALID for a bad device, BITSORT_ERR_NOMEM on failure
- * to allocate its fixed scratch. *ctx receives the handle. */
+ * to allocate its fixed scratch. *ctx receives the handle.
+ * Environment read here:
+ *   BITSORT_TUNE_CACHE=path  load the tuned table written by
+ *                            bitsort_tune_save (a missing or unreadable file
+ *                            is noted in bitsort_last_error and ignored);
+ *   BITSORT_FORCE_PATH=fused|partition|global  take that path for every
+ *                            single sort of the context, tuned or not (the
+ *                            size rules still apply: no fused slice beyond
+ *                            2^20 values); other values are ignored.
+ * Every sorting call opens an NVTX range named after itself (host side, the
+ * call's enqueue; no cost unless a profiler is attached). */
 bitsort_status_t bitsort_ctx_create(int device, bitsort_ctx_t **ctx);
 
 /* Synchronise the device and free everything the context owns. */

@@ -90,6 +90,15 @@ static bitsort_status_t ctx_alloc_fixed(bitsort_ctx *c) {
     return BITSORT_OK;
 }
 
+// "fused", "partition" or "global" (BITSORT_FORCE_PATH) -> a path; else 0
+static int parse_path(const char *s) {
+    if (!s) return 0;
+    if (!strcmp(s, "fused")) return BITSORT_PATH_FUSED;
+    if (!strcmp(s, "partition")) return BITSORT_PATH_PARTITION;
+    if (!strcmp(s, "global")) return BITSORT_PATH_GLOBAL;
+    return 0;
+}
+
 extern "C" bitsort_status_t bitsort_ctx_create(int device, bitsort_ctx_t **out) {
     if (!out) return BITSORT_ERR_INVALID;
     *out = nullptr;
@@ -120,6 +129,14 @@ extern "C" bitsort_status_t bitsort_ctx_create(int device, bitsort_ctx_t **out) 
         delete c;
         return st;
     }
+    // environment: a tuned table saved by bitsort_tune_save, and a path
+    // forced for every single sort (debugging, comparisons)
+    const char *cache = getenv("BITSORT_TUNE_CACHE");
+    if (cache && cache[0] && bitsort_tune_load(c, cache) != BITSORT_OK) {
+        snprintf(g_last_error, sizeof(g_last_error), "BITSORT_TUNE_CACHE: %s not loaded", cache);
+        if (getenv("BITSORT_VERBOSE")) fprintf(stderr, "bitsort: %s\n", g_last_error);
+    }
+    c->force_path = parse_path(getenv("BITSORT_FORCE_PATH"));
     *out = c;
     return BITSORT_OK;
 }
@@ -223,8 +240,9 @@ bsx_config bsx_default_config(int sms, uint64_t n, uint64_t M) {
 bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M) {
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->table.find(std::make_pair(ilog2_ceil(n), ilog2_ceil(M)));
-    if (it != c->table.end()) return it->second;
-    return bsx_default_config(c->sms, n, M);
+    bsx_config cfg = it != c->table.end() ? it->second : bsx_default_config(c->sms, n, M);
+    if (c->force_path) cfg.path = (bitsort_path_t)c->force_path;   // the size rules still apply (bsx_sanitize)
+    return cfg;
 }
 
 // Make a configuration valid for (n, M): the slice count within bounds, the
@@ -604,6 +622,7 @@ bitsort_status_t bsx_validate(const uint32_t *keys, uint64_t n, uint32_t max_val
 
 extern "C" bitsort_status_t bitsort_ex(bitsort_ctx_t *c, const uint32_t *keys, uint64_t n, uint32_t max_value,
                                        uint32_t *out, bitsort_result_t *d_result, bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_ex");
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     bitsort_status_t st = bsx_validate(keys, n, max_value, out);
@@ -619,6 +638,7 @@ extern "C" bitsort_status_t bitsort_ex(bitsort_ctx_t *c, const uint32_t *keys, u
 extern "C" bitsort_status_t bitsort_i32(bitsort_ctx_t *c, const int32_t *keys, uint64_t n, int32_t min_value,
                                         int32_t max_value, int32_t *out, bitsort_result_t *d_result,
                                         bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_i32");
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     if (min_value > max_value) return BITSORT_ERR_INVALID;
@@ -641,6 +661,7 @@ extern "C" bitsort_status_t bitsort_i32(bitsort_ctx_t *c, const int32_t *keys, u
 
 extern "C" bitsort_status_t bitsort_host(bitsort_ctx_t *c, const uint32_t *h_keys, uint64_t n, uint32_t max_value,
                                          uint32_t *h_out, bitsort_result_t *h_result, bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_host");
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     if (n > 0 && (!h_keys || !h_out)) return BITSORT_ERR_INVALID;
@@ -912,6 +933,7 @@ static bitsort_status_t ensure_flush(bitsort_ctx *c) {
 
 extern "C" bitsort_status_t bitsort_autotune(bitsort_ctx_t *c, const uint32_t *keys, uint32_t *out, uint64_t n,
                                              uint32_t max_value, bitsort_config_t *best_out) {
+    bsx_range nvtx_range_("bitsort_autotune");
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     bitsort_status_t st = bsx_validate(keys, n, max_value, out);

@@ -256,6 +256,7 @@ bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, siz
 
 extern "C" bitsort_status_t bitsort_batch_plan_create(bitsort_ctx_t *c, const bitsort_desc_t *descs, size_t count,
                                                       bitsort_batch_plan_t **plan) {
+    bsx_range nvtx_range_("bitsort_batch_plan_create");
     if (!plan) return BITSORT_ERR_INVALID;
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
@@ -275,6 +276,7 @@ bitsort_status_t bsx_plan_launch_direct(bitsort_batch_plan *pl, cudaStream_t s) 
 }
 
 extern "C" bitsort_status_t bitsort_batch_plan_launch(bitsort_batch_plan_t *pl, bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_batch_plan_launch");
     if (!pl) return BITSORT_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (cudaSetDevice(pl->ctx->device) != cudaSuccess) return BITSORT_ERR_CUDA;
@@ -355,6 +357,7 @@ const bitsort_result_t *bsx_plan_results_ptr(const bitsort_batch_plan *pl) { ret
 
 extern "C" bitsort_status_t bitsort_batched(bitsort_ctx_t *c, const bitsort_desc_t *descs, size_t count,
                                             bitsort_result_t *d_results, bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_batched");
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;
@@ -403,6 +406,7 @@ extern "C" bitsort_status_t bitsort_get_batch_config(bitsort_ctx_t *c, bitsort_c
 
 extern "C" bitsort_status_t bitsort_batch_autotune(bitsort_ctx_t *c, const bitsort_desc_t *descs, size_t count,
                                                    bitsort_config_t *best_out) {
+    bsx_range nvtx_range_("bitsort_batch_autotune");
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;

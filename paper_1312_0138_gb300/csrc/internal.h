@@ -8,6 +8,7 @@
 #include <utility>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/bitsort.h"
 #include "engine.h"
@@ -30,6 +31,7 @@ struct bsx_config {
 struct bitsort_ctx {
     int device = 0;
     int sms = 0;
+    int force_path = 0;   // BITSORT_FORCE_PATH at creation: a bitsort_path_t for every single sort, 0 = none
     size_t l2_bytes = 0;
     uint32_t smem_optin = 0;
     uint64_t wait_limit_ns = 0;
@@ -92,6 +94,15 @@ struct bitsort_ctx {
         return b;
     }
     std::atomic<uint64_t> launches{0};
+};
+
+// NVTX range over a library call (host side: the call's enqueue), for
+// profilers that filter or group by range; a no-op when no tool is attached.
+struct bsx_range {
+    explicit bsx_range(const char *name) { nvtxRangePushA(name); }
+    ~bsx_range() { nvtxRangePop(); }
+    bsx_range(const bsx_range &) = delete;
+    bsx_range &operator=(const bsx_range &) = delete;
 };
 
 bitsort_status_t bsx_check(cudaError_t e);

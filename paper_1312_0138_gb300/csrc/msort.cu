@@ -485,6 +485,7 @@ void bsx_multiset_free(bitsort_ctx *c) {
 extern "C" bitsort_status_t bitsort_multiset(bitsort_ctx_t *c, const uint32_t *keys, uint64_t n, uint32_t max_value,
                                              uint32_t split_bits, uint32_t *out, bitsort_result_t *d_result,
                                              bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_multiset");
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     return multiset_run(c, keys, n, 0u, max_value, split_bits, out, d_result,
@@ -494,6 +495,7 @@ extern "C" bitsort_status_t bitsort_multiset(bitsort_ctx_t *c, const uint32_t *k
 extern "C" bitsort_status_t bitsort_multiset_i32(bitsort_ctx_t *c, const int32_t *keys, uint64_t n,
                                                  int32_t min_value, int32_t max_value, uint32_t split_bits,
                                                  int32_t *out, bitsort_result_t *d_result, bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_multiset_i32");
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     if (min_value > max_value) return BITSORT_ERR_INVALID;

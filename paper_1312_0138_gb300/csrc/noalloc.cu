@@ -77,6 +77,7 @@ static bitsort_status_t device_setup(int dev, DeviceState **out) {
 
 extern "C" bitsort_status_t bitsort_noalloc(const uint32_t *keys, uint64_t n, uint32_t max_value, uint32_t *out,
                                             bitsort_result_t *d_result, bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_noalloc");
     if (!d_result) return BITSORT_ERR_INVALID;
     bitsort_status_t st = bsx_validate(keys, n, max_value, out);
     if (st != BITSORT_OK) return st;

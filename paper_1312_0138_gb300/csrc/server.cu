@@ -322,6 +322,7 @@ extern "C" bitsort_status_t bitsort_server_create(int device, uint64_t budget_by
 
 extern "C" bitsort_status_t bitsort_server_submit(bitsort_server_t *sv, const uint32_t *keys, uint64_t n,
                                                   uint32_t max_value, uint32_t *out, uint64_t *ticket) {
+    bsx_range nvtx_range_("bitsort_server_submit");
     if (!sv || !ticket) return BITSORT_ERR_INVALID;
     bitsort_status_t st = bsx_validate(keys, n, max_value, out);
     if (st != BITSORT_OK) return st;

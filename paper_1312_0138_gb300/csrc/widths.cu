@@ -161,16 +161,19 @@ void bsx_widths_free(bitsort_ctx *c) {
 
 extern "C" bitsort_status_t bitsort_u16(bitsort_ctx_t *c, const uint16_t *keys, uint64_t n, uint16_t max_value,
                                         uint16_t *out, bitsort_result_t *d_result, bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_u16");
     return small_sort<uint16_t>(c, keys, n, max_value, out, d_result, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" bitsort_status_t bitsort_u8(bitsort_ctx_t *c, const uint8_t *keys, uint64_t n, uint8_t max_value,
                                        uint8_t *out, bitsort_result_t *d_result, bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_u8");
     return small_sort<uint8_t>(c, keys, n, max_value, out, d_result, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" bitsort_status_t bitsort_u64(bitsort_ctx_t *c, const uint64_t *keys, uint64_t n, uint64_t max_value,
                                         uint64_t *out, bitsort_result_t *d_result, bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_u64");
     if (!c) c = bsx_default_ctx();
     if (!c) return BITSORT_ERR_CUDA;
     if (max_value > 0xFFFFFFFFull) return BITSORT_ERR_INVALID;
