@@ -34,6 +34,11 @@ MUTANTS = [
      "for (uint64_t i = 0; i < n1; ++i) a[n0 + i] = ones[n1 - 1 - i];"),
     ("paper_negatives_last", "for (uint64_t i = 0; i < nm; ++i) a[i] = (int32_t)neg[i];\n        for (uint64_t i = 0; i < np; ++i) a[nm + i] = (int32_t)pos[i];",
      "for (uint64_t i = 0; i < np; ++i) a[i] = (int32_t)pos[i];\n        for (uint64_t i = 0; i < nm; ++i) a[np + i] = (int32_t)neg[i];"),
+    ("i32_shift_back_dropped", "out[i] = (int32_t)((int64_t)((uint32_t *)out)[i] + (int64_t)min_value);",
+     "out[i] = (int32_t)((int64_t)((uint32_t *)out)[i]);"),
+    ("i32_below_clamped_into_range", "d = (int64_t)max_value - (int64_t)min_value + 1; }", "d = 0; }"),
+    ("i32_offset_wraps_32_bits", "int64_t d = (int64_t)keys[i] - (int64_t)min_value;",
+     "int64_t d = (int64_t)(int32_t)((uint32_t)keys[i] - (uint32_t)min_value);"),
     ("u64_emit_truncated", "out[k] = w * 32u + b;", "out[k] = (uint32_t)(w * 32u + b);"),
     ("u64_range_check_32_bits", "uint64_t x = keys[i];", "uint64_t x = (uint32_t)keys[i];"),
     ("bin_repl_lsb_first", "out[15 - d] = ((bits >> d) & 1u) ? '1' : '0';",
