@@ -34,6 +34,11 @@ MUTANTS = [
      "for (uint64_t i = 0; i < n1; ++i) a[n0 + i] = ones[n1 - 1 - i];"),
     ("paper_negatives_last", "for (uint64_t i = 0; i < nm; ++i) a[i] = (int32_t)neg[i];\n        for (uint64_t i = 0; i < np; ++i) a[nm + i] = (int32_t)pos[i];",
      "for (uint64_t i = 0; i < np; ++i) a[i] = (int32_t)pos[i];\n        for (uint64_t i = 0; i < nm; ++i) a[np + i] = (int32_t)neg[i];"),
+    ("bitmap_words_floor", "uint64_t words = (M + 31u) / 32u;", "uint64_t words = M / 32u;"),
+    ("status_precedence_swapped", "if (out_of_range) return ORACLE_KEY_RANGE;\n    if (k < n) return ORACLE_DUPLICATE;",
+     "if (k < n) return ORACLE_DUPLICATE;\n    if (out_of_range) return ORACLE_KEY_RANGE;"),
+    ("paper_split_msb_first", "if (a[i] & (1u << k)) { ones[n1] = a[i]; ++n1; }",
+     "if (a[i] & (1u << (nbits - 1 - k))) { ones[n1] = a[i]; ++n1; }"),
     ("i32_shift_back_dropped", "out[i] = (int32_t)((int64_t)((uint32_t *)out)[i] + (int64_t)min_value);",
      "out[i] = (int32_t)((int64_t)((uint32_t *)out)[i]);"),
     ("i32_below_clamped_into_range", "d = (int64_t)max_value - (int64_t)min_value + 1; }", "d = 0; }"),
