@@ -69,3 +69,23 @@ def test_product_does_not_import_the_oracle():
                 assert "oracle" not in re.sub(r"(#|//).*", "", src).lower() or f == "__init__.py" and \
                     "import oracle" not in src, f
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_binding_refuses_host_tensors_and_missing_gpu(lib_path):
+    # the device entry points take device memory only: a CPU tensor is an
+    # error before anything is called, never a silent host computation
+    import torch
+    import paper_1312_0138_gb300 as p
+    p.load(lib_path)
+    keys = torch.arange(8, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        p.bitsort(keys, 7)
+    with pytest.raises(TypeError):
+        p._ptr(keys.to(torch.float32).cuda() if torch.cuda.is_available() else 3.0)
+    assert p._host_ptr(keys) == keys.data_ptr()
+    with pytest.raises(TypeError):
+        p._host_ptr(keys.to(torch.float32))
+    if not torch.cuda.is_available():
+        # without a GPU a context cannot be made: the call fails loudly
+        with pytest.raises(p.BitsortError):
+            p.Context(0)
