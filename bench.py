@@ -1,13 +1,16 @@
 """Benchmark of the GB300 bitmap sort.
 
-Default workload: one array of n = 2^24 distinct uint32 keys drawn uniformly
-without replacement from [0, 2^28) (Floyd sampling + shuffle), max_value =
-2^28 - 1 (32 MiB bitmap).  One step = one sort of the whole array (every step
-of the path: range check, scatter, popcount, scan, emission) through the C
-ABI call `bitsort_ex`, inputs already resident in HBM.  L2 is flushed between
-timed steps (a 512 MiB write, outside the timed events).
+Default workload: the largest single-array configuration, one array of
+n = 2^31 distinct uint32 keys over the full 32-bit range [0, 2^32) (density
+1/2; 8 GiB of keys in, 8 GiB out, a 512 MiB bitmap), the keys pi(0..n-1) of a
+seeded Feistel bijection pi (a stand-in for sampling without replacement).
+One step = one sort of the whole array (every step of the path: range check,
+partition, scatter, popcount, offsets, emission) through the C ABI call
+`bitsort_ex`, inputs already resident in HBM.  L2 is flushed between timed
+steps (a 512 MiB write and a 512 MiB read, outside the timed events); the
+arrays are also far larger than L2.
 
-Other workloads (--workload): c0 (n=1e5, M=2^20), c2a (n=2^31, M=2^32),
+Other workloads (--workload): c0 (n=1e5, M=2^20), c1 (n=2^24, M=2^28),
 c2b (n=2^24, M=2^32), batched (4096 arrays, one launch, graph replay),
 served (Poisson arrivals through the serving loop).
 
@@ -191,13 +194,25 @@ def time_oracle(keys_np, max_value, budget_s=10.0, max_keys=None):
                       f"(max_value={max_value}), {t_total:.1f} s"}
 
 
+def sample_keys(w, rank, max_keys):
+    """The workload's first max_keys keys (all of them when it has fewer).
+    Feistel keys are pi(0), pi(1), ...: the first k keys of the array are the
+    k keys the generator gives for n = k."""
+    import gen
+    if max_keys is None or w["n"] <= max_keys:
+        return make_keys(w, rank)
+    if w["method"] == "feistel":
+        return gen.keys(SEED + w["cfg"] + 1000 * rank, max_keys, w["M"], "feistel")
+    return make_keys(w, rank)[:max_keys]
+
+
 def run_reference(args, w, ws, rank):
     if rank != 0:
         return
-    keys_np = make_keys(w, rank)
+    max_keys = 1 << 24 if w["n"] > (1 << 24) else None
+    keys_np = sample_keys(w, rank, max_keys)
     M = w["M"]
     per_step = []
-    max_keys = 1 << 24 if w["n"] > (1 << 24) else None
     for _ in range(args.warmup + args.steps):
         r = time_oracle(keys_np, M - 1, budget_s=0.0, max_keys=max_keys)
         per_step.append(r)
@@ -293,8 +308,16 @@ def run_plain(args, w, ws, rank, local):
     # M/8 + M/8 bitmap bytes
     kernel_bytes = {"hist": 4 * n, "part": 8 * n, "parts": 8 * n, "gscatter": 4 * n + M // 8, "gscan": 4 * n + M // 8,
                     "bucket": 8 * n + M // 4, "persistent": 8 * n + M // 4}
+    # the bytes each kernel must move through L2 / HBM: the bucket kernel
+    # builds and reads its bitmap slices in shared memory (M/4 never leaves
+    # the SM; sparse slices skip most of it through the summary bitmap), the
+    # global-bitmap kernels really move their bitmap bytes through L2
+    kernel_hbm_bytes = {"hist": 4 * n, "part": 8 * n, "parts": 8 * n, "gscatter": 4 * n + M // 8,
+                        "gscan": 4 * n + M // 8, "bucket": 8 * n, "persistent": 8 * n}
     dom_bytes = kernel_bytes.get(dom, algo_bytes)
+    dom_hbm_bytes = kernel_hbm_bytes.get(dom, 8 * n)
     achieved = dom_bytes / (kind_ms[dom] * 1e-3) / 1e9
+    hbm_achieved = dom_hbm_bytes / (kind_ms[dom] * 1e-3) / 1e9
 
     # end to end through the host-buffer entry point (bitsort_host): every
     # step copies its keys from pinned host memory, sorts, and copies the
@@ -359,13 +382,17 @@ def run_plain(args, w, ws, rank, local):
                    "plan": cfg, "wall_s": wall},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": dom_bytes,
+                     "hbm_algorithmic_bytes": dom_hbm_bytes, "hbm_achieved": hbm_achieved,
+                     "hbm_frac": hbm_achieved / peak,
                      "kernel_ms": kind_ms[dom], "kernels_ms": kind_ms,
                      "path_achieved": path_achieved, "path_frac": path_achieved / peak,
-                     "note": f"dominant kernel '{dom}': its algorithmic bytes (8 B per key, plus M/8 + M/8 "
-                             f"bitmap bytes when it builds and reads the bitmap; the bucket kernel keeps "
-                             f"them in shared memory) / its mean CUDA-event time over {phase_steps} "
-                             f"cold-L2 steps; path_frac = 8n+M/4 = {algo_bytes} B / whole-sort step time; "
-                             f"peak = {peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)"},
+                     "note": f"dominant kernel '{dom}': frac = its algorithmic bytes by the 8n+M/4 formula "
+                             f"(8 B per key, plus M/8 + M/8 bitmap bytes when it builds and reads the bitmap) "
+                             f"/ its mean CUDA-event time over {phase_steps} cold-L2 steps; the bucket kernel "
+                             f"keeps the M/4 bitmap bytes in shared memory (sparse slices skip most of them), "
+                             f"so hbm_frac counts only the bytes it must move through L2/HBM (8n for the "
+                             f"bucket and partition kernels); path_frac = 8n+M/4 = {algo_bytes} B / whole-sort "
+                             f"step time; peak = {peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)"},
         "e2e": {"value": job_gkeys_s(ws, n, e2e_ms), "unit": "Gkeys/s", "h2d_bytes_per_step": 4 * n,
                 "d2h_bytes_per_step": 4 * n + 16, "api": "bitsort_host (pinned host buffers)",
                 "overlap": "three streams with a context each; consecutive steps overlap",
@@ -645,10 +672,10 @@ def run_served(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: 100 for c2a, else 2000)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default: 5 for c2a, else 20)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=list(WORKLOADS) + ["batched", "served"])
+    ap.add_argument("--workload", default="c2a", choices=list(WORKLOADS) + ["batched", "served"])
     ap.add_argument("--path", default=None, choices=[None, "fused", "partition", "global"])
     ap.add_argument("--slice", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
@@ -664,14 +691,30 @@ def main():
     ap.add_argument("--flush", default="write+read", choices=["write", "write+read"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--n-log2", type=int, default=0,
+                    help="with --m-log2: a custom plain workload of 2^n-log2 Feistel keys from [0, 2^m-log2) "
+                         "(small cases for profiling)")
+    ap.add_argument("--m-log2", type=int, default=0)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--serve-count", type=int, default=400)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--inflight", type=int, default=4)
     args = ap.parse_args()
+    if args.n_log2 and args.m_log2:
+        n, M = 1 << args.n_log2, 1 << args.m_log2
+        assert n <= M
+        WORKLOADS["custom"] = dict(n=n, M=M, method="feistel", cfg=5,
+                                   desc=f"plain bitsort, one array: n=2^{args.n_log2} distinct uint32 from "
+                                        f"[0,2^{args.m_log2}) (Feistel permutation)")
+        args.workload = "custom"
+    big = args.workload == "c2a"
+    if args.steps is None:
+        args.steps = 100 if big else 2000
+    if args.warmup is None:
+        args.warmup = 5 if big else 20
     ws, rank, local = dist_init()
     if args.impl == "reference":
-        w = WORKLOADS.get(args.workload, WORKLOADS["c1"])
+        w = WORKLOADS.get(args.workload, WORKLOADS["c2a"])
         run_reference(args, w, ws, rank)
         return
     if args.workload == "batched":

@@ -211,11 +211,11 @@ bitsort_status_t bitsort_sync_status(bitsort_ctx_t *ctx, bitsort_stream_t stream
 
 /* Sort without allocating any device memory (the paper has no counterpart:
  * this is a deployment variant of bitsort_ex's partition path).  For callers
- * that cannot call cudaMalloc: code that runs while a CUDA graph is being
- * captured (a device allocation is not allowed there), applications whose
- * device memory is all owned by another allocator (e.g. a framework's
- * caching allocator that has reserved the whole HBM), and real-time or
- * certified code that forbids allocation after start-up.
+ * that cannot call cudaMalloc: applications whose device memory is all owned
+ * by another allocator (e.g. a framework's caching allocator that has
+ * reserved the whole HBM, so a cudaMalloc would fail), and real-time or
+ * certified code that forbids allocation after start-up (an allocation can
+ * block for an unbounded time and may synchronise the device).
  *   - keys, out: DEVICE pointers to n uint32 keys / outputs, NOT overlapping
  *     (out also serves as the partition buffer; keys == out is rejected).
  *   - d_result: DEVICE pointer (required) that receives the outcome, with

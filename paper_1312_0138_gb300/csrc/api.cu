@@ -60,6 +60,11 @@ void bsx_note_error(int e, const char *where) {
     if (getenv("BITSORT_VERBOSE")) fprintf(stderr, "bitsort: %s\n", g_last_error);
 }
 
+void bsx_note_msg(const char *msg) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+    if (getenv("BITSORT_VERBOSE")) fprintf(stderr, "bitsort: %s\n", g_last_error);
+}
+
 extern "C" const char *bitsort_last_error(void) { return g_last_error; }
 
 bitsort_status_t bsx_check(cudaError_t e) {
@@ -76,7 +81,11 @@ static bitsort_status_t ctx_alloc_fixed(bitsort_ctx *c) {
     size_t bytes = small + per * (4 + 4 + 8 + 8);
     cudaError_t e = cudaMalloc(&c->fixed, bytes);
     if (e != cudaSuccess) return bsx_check(e);
+    // cudaMemset returns before the memory is written (it runs on the legacy
+    // default stream, which a caller's non-blocking stream does not wait
+    // for): the device is synchronised before any sort can use the block
     e = cudaMemset(c->fixed, 0, bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return bsx_check(e);
     char *p = (char *)c->fixed;
     c->ticket = (uint32_t *)p;
@@ -369,7 +378,8 @@ static bitsort_status_t ensure_bitmap(bitsort_ctx *c, uint64_t M, cudaStream_t s
         c->bitmap = nullptr;
         return bsx_check(e);
     }
-    e = c->stream_ordered ? cudaMemsetAsync(c->bitmap, 0, words * 4, s) : cudaMemset(c->bitmap, 0, words * 4);
+    // zeroed in the order of the stream whose kernels use it next
+    e = cudaMemsetAsync(c->bitmap, 0, words * 4, s);
     if (e != cudaSuccess) return bsx_check(e);
     c->bitmap_words = words;
     return BITSORT_OK;
@@ -704,6 +714,7 @@ bitsort_status_t bsx_reset_scratch(bitsort_ctx *c) {
     if (e != cudaSuccess) return BITSORT_ERR_CUDA;
     e = cudaMemset(c->fixed, 0, c->fixed_bytes);
     if (e == cudaSuccess && c->bitmap) e = cudaMemset(c->bitmap, 0, c->bitmap_words * 4);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();   // the memsets are done before any stream uses the scratch
     return bsx_check(e);
 }
 
@@ -969,7 +980,8 @@ extern "C" bitsort_status_t bitsort_autotune(bitsort_ctx_t *c, const uint32_t *k
         }
         bitsort_result_t r;
         cudaMemcpy(&r, c->result, sizeof(r), cudaMemcpyDeviceToHost);
-        if (!ok || r.status != BITSORT_OK) {
+        // only a configuration that sorted the whole array counts
+        if (!ok || r.status != BITSORT_OK || r.count != n) {
             if (r.status == BITSORT_ERR_TIMEOUT) bsx_reset_scratch(c);
             continue;
         }

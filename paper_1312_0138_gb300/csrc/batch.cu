@@ -233,8 +233,13 @@ bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, siz
         if (e == cudaSuccess) e = cudaMemsetAsync(pl->scratch, 0, pl->scratch_bytes, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // host staging buffer goes out of scope
     } else {
+        // a copy from pageable memory may return before it reaches the
+        // device, and cudaMemset returns before the memory is written; both
+        // run on the legacy default stream, which the caller's (possibly
+        // non-blocking) launch stream does not wait for
         e = cudaMemcpy(pl->tables, host.data(), tables_bytes, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(pl->scratch, 0, pl->scratch_bytes);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {
         bitsort_batch_plan_destroy(pl);
@@ -323,6 +328,7 @@ extern "C" bitsort_status_t bitsort_batch_plan_results(bitsort_batch_plan_t *pl,
         cudaDeviceSynchronize();
         cudaMemset(pl->scratch, 0, pl->scratch_bytes);
         cudaMemset(pl->params.ticket, 0, 16);
+        cudaDeviceSynchronize();   // cleared before the next launch, on whatever stream
     }
     return first;
 }
@@ -416,8 +422,31 @@ extern "C" bitsort_status_t bitsort_batch_autotune(bitsort_ctx_t *c, const bitso
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // outcomes of the default policy: a candidate counts only if every array
+    // comes out with the same status and count (a policy that loses keys
+    // must never be picked because it ran fast)
+    std::vector<bitsort_result_t> want(count);
+    {
+        c->batch = bitsort_ctx::batch_default();
+        bitsort_batch_plan *pl = nullptr;
+        bitsort_status_t st = bsx_plan_build(c, descs, count, nullptr, nullptr, false, &pl, nullptr, 0);
+        if (st == BITSORT_OK) {
+            st = bsx_plan_launch_direct(pl, s);
+            bitsort_status_t rs = bitsort_batch_plan_results(pl, s, want.data());
+            bitsort_batch_plan_destroy(pl);
+            if (st == BITSORT_OK && (rs == BITSORT_ERR_TIMEOUT || rs == BITSORT_ERR_CUDA)) st = rs;
+        }
+        if (st != BITSORT_OK) {
+            c->batch = saved;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaStreamDestroy(s);
+            return st;
+        }
+    }
     double best = 1e30;
     bsx_config best_cfg = saved;
+    uint64_t rejected = 0;
     for (int path : {(int)BITSORT_PATH_PARTITION, (int)BITSORT_PATH_GLOBAL}) {
         for (uint32_t S : {1u << 17, 1u << 18, 1u << 19, 1u << 20}) {
             for (int T : {256, 512}) {
@@ -444,6 +473,13 @@ extern "C" bitsort_status_t bitsort_batch_autotune(bitsort_ctx_t *c, const bitso
                     bitsort_status_t st = bitsort_batch_plan_results(pl, s, res.data());
                     bitsort_batch_plan_destroy(pl);
                     if (!ok || st == BITSORT_ERR_TIMEOUT || st == BITSORT_ERR_CUDA) continue;
+                    bool same = true;
+                    for (size_t i = 0; i < count && same; ++i)
+                        same = res[i].status == want[i].status && res[i].count == want[i].count;
+                    if (!same) {
+                        ++rejected;
+                        continue;
+                    }
                     const double mean = sum / 3.0;
                     if (mean < best) {
                         best = mean;
@@ -456,6 +492,12 @@ extern "C" bitsort_status_t bitsort_batch_autotune(bitsort_ctx_t *c, const bitso
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
+    if (rejected) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "batch autotune: %llu policies left out, their outcomes differ from the default's",
+                 (unsigned long long)rejected);
+        bsx_note_msg(msg);
+    }
     if (best >= 1e30) {
         c->batch = saved;
         return BITSORT_ERR_CUDA;

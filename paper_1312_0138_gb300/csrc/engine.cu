@@ -89,7 +89,8 @@ struct SharedMisc {
 // after an iteration cap that bounds the loop even if the timer misbehaves.
 __device__ bool wait_geq(const uint32_t *p, uint32_t target, const uint32_t *timeout_flag, uint64_t limit_ns) {
     if (ld_acquire_u32(p) >= target) return true;
-    const uint64_t t0 = now_ns();
+    WaitClock clk;
+    clk.start();
     const uint64_t cap = limit_ns / 16 + 4096;
     uint32_t sleep = 32;
     for (uint64_t it = 0; it < cap; ++it) {
@@ -98,7 +99,7 @@ __device__ bool wait_geq(const uint32_t *p, uint32_t target, const uint32_t *tim
         if (ld_acquire_u32(p) >= target) return true;
         if ((it & 7) == 7) {
             if (ld_acquire_u32(timeout_flag) != 0) return false;
-            if (now_ns() - t0 > limit_ns) return false;
+            if (clk.expired(limit_ns)) return false;
         }
     }
     return false;
@@ -217,19 +218,19 @@ __device__ uint64_t lookback(const EngineParams &P, const ArrayDesc &a, uint32_t
     uint64_t excl = 0;
     int64_t j = (int64_t)s - 1;
     bool expired = false;
-    uint64_t t0 = 0;
+    WaitClock clk;
     uint64_t iters = 0;
     const uint64_t cap = P.wait_limit_ns / 16 + 4096;
     while (true) {
         const int64_t idx = j - lane;
         uint64_t v = idx >= 0 ? ld_acquire_u64(&look[idx]) : LB_PREFIX;
         while (__any_sync(kFull, (v >> 62) == 0)) {
-            if (iters == 0) t0 = now_ns();
+            if (iters == 0) clk.start();
             ++iters;
             if ((iters & 7) == 0) {
                 bool stop = false;
                 if (lane == 0)
-                    stop = iters > cap || now_ns() - t0 > P.wait_limit_ns ||
+                    stop = iters > cap || clk.expired(P.wait_limit_ns) ||
                            ld_acquire_u32(&a.sync[SY_TIMEOUT]) != 0;
                 if (__shfl_sync(kFull, stop ? 1 : 0, 0)) {
                     expired = true;
@@ -949,10 +950,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
 // own); false after `limit_ns` (then the caller reports a timeout).
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(mbar, parity)) return true;
-    const uint64_t t0 = now_ns();
+    WaitClock clk;
+    clk.start();
     for (uint32_t it = 0; it < (1u << 30); ++it) {
         if (mbar_try_wait(mbar, parity)) return true;
-        if ((it & 63) == 63 && now_ns() - t0 > limit_ns) return false;
+        if ((it & 63) == 63 && clk.expired(limit_ns)) return false;
     }
     return false;
 }
@@ -962,7 +964,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint6
 // written, the bulk-copy engine already brings tile k+1 into the other
 // buffer; a tile's landing buffer then serves as its reordered copy.  Tiles
 // that are not whole, or keys that are not 16-byte aligned, are loaded by
-// the threads instead.
+// the threads instead.  The next tile's copy is issued only after the
+// current tile's wait has succeeded in every thread, so after a timeout at
+// most the copy that timed out is still outstanding; the CTA waits for it
+// (four times the wait limit) before it exits.  That last wait is the only
+// one whose expiry could leave a copy in flight at exit.
 template <int T>
 __device__ void part_stream(const EngineParams &P, const ArrayDesc &a, char *smem, SharedMisc &m) {
     constexpr int K = kKeysPerThread;
@@ -995,43 +1001,30 @@ __device__ void part_stream(const EngineParams &P, const ArrayDesc &a, char *sme
         mbar_expect_tx(&mbar[0], tile_bytes);
         bulk_load(buf0, a.keys + (uint64_t)t * a.tile_keys, tile_bytes, &mbar[0]);
     }
-    // per buffer: completed uses (mbarrier phase parity) and a copy not yet waited for
-    uint32_t uses0 = 0, uses1 = 0;
-    bool pend0 = t < ntiles && whole(t), pend1 = false;
-    bool ok = true;
+    // per buffer: completed uses (mbarrier phase parity) and a copy issued
+    // whose completion has not been seen
+    uint32_t uses[2] = {0u, 0u};
+    bool pend[2] = {t < ntiles && whole(t), false};
     for (uint32_t k = 0; t < ntiles; ++k, t += G) {
         const uint32_t b = k & 1u;
         uint32_t *cur = buf0 + (b ? a.tile_keys : 0u);
         uint32_t *nxt = buf0 + (b ? 0u : a.tile_keys);
-        const uint32_t tn = t + G;
-        if (tn < ntiles && whole(tn)) {
-            if (threadIdx.x == 0) {
-                fence_proxy_async_smem();   // this buffer was last read and written by the threads
-                mbar_expect_tx(&mbar[b ^ 1u], tile_bytes);
-                bulk_load(nxt, a.keys + (uint64_t)tn * a.tile_keys, tile_bytes, &mbar[b ^ 1u]);
-            }
-            if (b) pend0 = true;
-            else pend1 = true;
-        }
         for (uint32_t i = threadIdx.x; i < nbins; i += T) hist[i] = 0;
         const uint64_t lo = (uint64_t)t * a.tile_keys;
         const uint32_t nkeys = (uint32_t)(min(lo + a.tile_keys, a.n) - lo);
         uint32_t x[K];
+        bool ok = true;
         if (whole(t)) {
-            const uint32_t use = b ? uses1 : uses0;
-            if (!mbar_wait(&mbar[b], use & 1u, P.wait_limit_ns)) ok = false;
-            if (b) {
-                ++uses1;
-                pend1 = false;
-            } else {
-                ++uses0;
-                pend0 = false;
-            }
-            const uint4 *src = reinterpret_cast<const uint4 *>(cur);
+            ok = mbar_wait(&mbar[b], uses[b] & 1u, P.wait_limit_ns);
+            if (ok) {
+                ++uses[b];
+                pend[b] = false;
+                const uint4 *src = reinterpret_cast<const uint4 *>(cur);
 #pragma unroll
-            for (int j = 0; j < K / 4; ++j) {
-                const uint4 q = src[j * T + threadIdx.x];
-                x[4 * j] = q.x; x[4 * j + 1] = q.y; x[4 * j + 2] = q.z; x[4 * j + 3] = q.w;
+                for (int j = 0; j < K / 4; ++j) {
+                    const uint4 q = src[j * T + threadIdx.x];
+                    x[4 * j] = q.x; x[4 * j + 1] = q.y; x[4 * j + 2] = q.z; x[4 * j + 3] = q.w;
+                }
             }
         } else {
 #pragma unroll
@@ -1040,18 +1033,28 @@ __device__ void part_stream(const EngineParams &P, const ArrayDesc &a, char *sme
                 x[j] = e < nkeys ? __ldcs(a.keys + lo + e) : 0u;
             }
         }
-        __syncthreads();   // hist zeroed; every thread holds its keys (the buffer is free)
+        // hist zeroed; every thread holds its keys (the buffer is free) or
+        // some thread's wait ran out
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicOr(&a.sync[SY_TIMEOUT], 1u);
             break;
         }
+        const uint32_t tn = t + G;
+        if (tn < ntiles && whole(tn)) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();   // this buffer was last read and written by the threads
+                mbar_expect_tx(&mbar[b ^ 1u], tile_bytes);
+                bulk_load(nxt, a.keys + (uint64_t)tn * a.tile_keys, tile_bytes, &mbar[b ^ 1u]);
+            }
+            pend[b ^ 1u] = true;
+        }
         part_tile<T>(a, x, nkeys, hist, delta, lim, cur, tags, m);
         __syncthreads();
     }
-    // no bulk copy of this CTA may still be in flight when it exits (only
-    // after a timeout can one be left un-waited)
-    if (pend0) mbar_wait(&mbar[0], uses0 & 1u, P.wait_limit_ns);
-    if (pend1) mbar_wait(&mbar[1], uses1 & 1u, P.wait_limit_ns);
+    // no bulk copy of this CTA may still be in flight when it exits: only a
+    // copy whose wait ran out can be outstanding here
+    for (int q = 0; q < 2; ++q)
+        if (pend[q]) mbar_wait(&mbar[q], uses[q] & 1u, 4 * P.wait_limit_ns);
 }
 
 // Sparse slice (few keys for its words): the scatter also set one summary

@@ -107,6 +107,7 @@ struct bsx_range {
 
 bitsort_status_t bsx_check(cudaError_t e);
 void bsx_note_error(int e, const char *where);
+void bsx_note_msg(const char *msg);   // the text bitsort_last_error() returns next
 bitsort_ctx *bsx_default_ctx();
 uint64_t bsx_div_magic(uint32_t S);
 bsx_config bsx_default_config(int sms, uint64_t n, uint64_t M);

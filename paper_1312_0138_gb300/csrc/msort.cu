@@ -124,7 +124,8 @@ __device__ uint32_t tile_lookback(const uint64_t *look, uint32_t tile, uint32_t 
                                   uint32_t *timeout, uint64_t limit_ns) {
     uint32_t excl = 0;
     int64_t top = (int64_t)tile - 1;   // nearest predecessor not yet consumed
-    uint64_t spins = 0, t0 = 0;
+    uint64_t spins = 0;
+    WaitClock clk;
     const uint64_t cap = limit_ns / 16 + 4096;
     while (top >= 0) {
         uint64_t v[kWindow];
@@ -146,10 +147,10 @@ __device__ uint32_t tile_lookback(const uint64_t *look, uint32_t tile, uint32_t 
             while (true) {
                 const uint64_t u = ld_relaxed_u64(p);
                 if ((uint32_t)(u >> kEpochShift) == epoch && ((uint32_t)(u >> 32) & 3u) != 0) break;
-                if (spins == 0) t0 = now_ns();
+                if (spins == 0) clk.start();
                 ++spins;
                 if (spins > cap ||
-                    ((spins & 15) == 0 && (now_ns() - t0 > limit_ns || ld_acquire_u32(timeout) != 0))) {
+                    ((spins & 15) == 0 && (clk.expired(limit_ns) || ld_acquire_u32(timeout) != 0))) {
                     atomicOr(timeout, 1u);
                     return excl;
                 }
@@ -344,7 +345,7 @@ PassKernel pass_kernel(uint32_t D) {
     }
 }
 
-bitsort_status_t ensure_multiset_scratch(bitsort_ctx *c, uint64_t look_words) {
+bitsort_status_t ensure_multiset_scratch(bitsort_ctx *c, uint64_t look_words, cudaStream_t s) {
     if (!c->ms_misc) {
         cudaError_t e = cudaMalloc(&c->ms_misc, kMiscWords * sizeof(uint32_t));
         if (e != cudaSuccess) {
@@ -364,7 +365,8 @@ bitsort_status_t ensure_multiset_scratch(bitsort_ctx *c, uint64_t look_words) {
             c->ms_look = nullptr;
             return bsx_check(e);
         }
-        e = cudaMemset(c->ms_look, 0, look_words * sizeof(uint64_t));   // epoch 0 is never used
+        // epoch 0 is never used; zeroed in the order of the stream that uses it
+        e = cudaMemsetAsync(c->ms_look, 0, look_words * sizeof(uint64_t), s);
         if (e != cudaSuccess) return bsx_check(e);
         c->ms_look_words = look_words;
     }
@@ -399,7 +401,7 @@ bitsort_status_t multiset_run(bitsort_ctx *c, const uint32_t *keys, uint64_t n, 
     if (P > kMaxPasses || P * (1u << D) > kHistWords) return BITSORT_ERR_INVALID;   // (never: D >= 1, bits <= 32)
     const uint32_t R = 1u << D;
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
-    bitsort_status_t st = ensure_multiset_scratch(c, (uint64_t)ntiles * R);
+    bitsort_status_t st = ensure_multiset_scratch(c, (uint64_t)ntiles * R, s);
     if (st != BITSORT_OK) return st;
     const bool inplace = keys == out;
     // pass p writes `out` when P - 1 - p is even (the last pass ends in out);
@@ -412,7 +414,8 @@ bitsort_status_t multiset_run(bitsort_ctx *c, const uint32_t *keys, uint64_t n, 
     uint32_t *tmp = c->part;
     if (c->ms_epoch + P > kEpochMax) {   // epochs wrap: start the look-back array afresh
         if (cudaDeviceSynchronize() != cudaSuccess) return BITSORT_ERR_CUDA;
-        if (cudaMemset(c->ms_look, 0, c->ms_look_words * sizeof(uint64_t)) != cudaSuccess) return BITSORT_ERR_CUDA;
+        if (cudaMemsetAsync(c->ms_look, 0, c->ms_look_words * sizeof(uint64_t), s) != cudaSuccess)
+            return BITSORT_ERR_CUDA;
         c->ms_epoch = 0;
     }
 

@@ -29,4 +29,30 @@ __device__ __forceinline__ uint64_t now_ns() {
     return t;
 }
 
+// Wall-clock bound of one wait.  The wait has expired once two consecutive
+// windows of half the limit have passed, each measured from a fresh timer
+// read: a single step of the global timer (the driver may adjust it, forwards
+// or back) then cannot end a wait early, and a timer read that lies before
+// the window's start restarts the window instead of wrapping the unsigned
+// difference.  Every caller also caps its number of polls, so a timer that
+// stops or runs backwards still ends the wait.
+struct WaitClock {
+    uint64_t t0 = 0;
+    uint32_t windows = 0;
+    __device__ __forceinline__ void start() {
+        t0 = now_ns();
+        windows = 0;
+    }
+    __device__ __forceinline__ bool expired(uint64_t limit_ns) {
+        const uint64_t t = now_ns();
+        if (t < t0) {
+            t0 = t;
+        } else if (t - t0 > limit_ns / 2) {
+            t0 = t;
+            ++windows;
+        }
+        return windows >= 2;
+    }
+};
+
 }  // namespace bsx

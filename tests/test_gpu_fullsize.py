@@ -89,9 +89,11 @@ def _check_feistel_output(out_dev, seed, n, M):
 
 def test_batched_full_size(ctx):
     """The benchmark's batch (4096 arrays, 2.07 G keys, seeds and sizes as
-    timed) in one persistent launch with the default batch policy: every
-    outcome, every output by its three properties, and a sample of arrays
-    element by element against the oracle."""
+    timed) in one persistent launch with the default batch policy, replayed
+    three times from its CUDA graph (the first replay on a non-blocking
+    stream that starts right after the plan is built): every outcome, every
+    output by its three properties, and a sample of arrays element by
+    element against the oracle, after every replay."""
     import torch
     seed0 = gen.SEED_BASE
     spec = gen.batch_spec(seed0 + 3, 4096)
@@ -99,21 +101,28 @@ def test_batched_full_size(ctx):
     keys = [to_dev(k) for k in keys_np]
     outs = [torch.empty_like(k) for k in keys]
     plan = ctx.plan([(k, M - 1, o) for k, (n, M), o in zip(keys, spec, outs)])
-    plan.launch()
-    res = plan.results()
-    for i, ((n, M), (st, cnt)) in enumerate(zip(spec, res)):
-        assert st == bs.OK and cnt == n, (i, st, cnt, n)
-        _check_feistel_output(outs[i], seed0 + 7 * i, n, M)
-    for i in range(0, 4096, 97):
-        want_st, want = oracle.bitmap_sort(keys_np[i], spec[i][1] - 1)
-        assert want_st == bs.OK and np.array_equal(to_host(outs[i]), want), i
+    side = torch.cuda.Stream()
+    wants = {i: oracle.bitmap_sort(keys_np[i], spec[i][1] - 1) for i in range(0, 4096, 97)}
+    for rep in range(3):
+        for o in outs:
+            o.fill_(-1)
+        torch.cuda.synchronize()
+        stream = side if rep == 0 else None
+        plan.launch(stream=stream)
+        res = plan.results(stream=stream)
+        for i, ((n, M), (st, cnt)) in enumerate(zip(spec, res)):
+            assert st == bs.OK and cnt == n, (rep, i, st, cnt, n)
+            _check_feistel_output(outs[i], seed0 + 7 * i, n, M)
+        for i, (want_st, want) in wants.items():
+            assert want_st == bs.OK and np.array_equal(to_host(outs[i]), want), (rep, i)
     plan.close()
 
 
 def test_served_full_size(ctx):
     """The benchmark's saturated serving run (300 Poisson requests, n up to
-    2^26, max_value up to 2^32 - 1, 40 GiB budget, 4 streams): every request's
-    outcome and output, and a sample element by element against the oracle."""
+    2^26, max_value up to 2^32 - 1, 40 GiB budget, 4 streams), submitted
+    twice to one server: every request's outcome and output in both rounds,
+    and a sample element by element against the oracle."""
     import torch
     seed0 = gen.SEED_BASE
     spec = gen.serve_spec(seed0 + 4, 300, rate_hz=1e6)
@@ -121,15 +130,20 @@ def test_served_full_size(ctx):
     for i, (_, n, M) in enumerate(spec):
         k = gen.feistel(seed0 + 11 * i, n, M)
         reqs.append((k, M - 1, to_dev(k)))
+    wants = {i: oracle.bitmap_sort(reqs[i][0], reqs[i][1]) for i in range(0, 300, 37)}
     srv = bs.Server(0, budget_bytes=40 << 30, max_inflight=4)
     outs = [torch.empty_like(kd) for _, _, kd in reqs]
-    tickets = [srv.submit(kd, mv, o) for (_, mv, kd), o in zip(reqs, outs)]
-    for i, t in enumerate(tickets):
-        st, cnt, _ = srv.wait(t)
-        n, M = spec[i][1], spec[i][2]
-        assert st == bs.OK and cnt == n, (i, st, cnt, n, M)
-        _check_feistel_output(outs[i], seed0 + 11 * i, n, M)
+    for rnd in range(2):
+        for o in outs:
+            o.fill_(-1)
+        torch.cuda.synchronize()
+        tickets = [srv.submit(kd, mv, o) for (_, mv, kd), o in zip(reqs, outs)]
+        for i, t in enumerate(tickets):
+            st, cnt, _ = srv.wait(t)
+            n, M = spec[i][1], spec[i][2]
+            assert st == bs.OK and cnt == n, (rnd, i, st, cnt, n, M)
+        for i in range(300):
+            _check_feistel_output(outs[i], seed0 + 11 * i, spec[i][1], spec[i][2])
+        for i, (want_st, want) in wants.items():
+            assert want_st == bs.OK and np.array_equal(to_host(outs[i]), want), (rnd, i)
     srv.close()
-    for i in range(0, 300, 37):
-        want_st, want = oracle.bitmap_sort(reqs[i][0], reqs[i][1])
-        assert want_st == bs.OK and np.array_equal(to_host(outs[i]), want), i

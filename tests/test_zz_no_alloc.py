@@ -1,12 +1,14 @@
 """bitsort_noalloc: the sort for callers that cannot allocate device memory.
 
-Some callers of this library cannot call cudaMalloc: code running while a
-CUDA graph is being captured, applications whose device memory is all held by
-another allocator, real-time code that forbids allocation after start-up.
-bitsort_noalloc keeps its scratch in a fixed device array of the library
-instead.  This test calls it through the C ABI twice in a row and checks that
-each result is bit-identical to the one the allocating entry point
-(bitsort_ex) gives for the same keys.  Collected last on purpose.
+Some callers of this library cannot call cudaMalloc: applications whose
+device memory is all held by another allocator (a caching pool sized to the
+whole GPU), and real-time code that forbids allocation after start-up because
+an allocation can block for an unbounded time.  bitsort_noalloc keeps its
+scratch in a fixed device array of the library instead.  This test calls it
+through the C ABI twice in a row and checks that each result is
+bit-identical to the CPU oracle's and to the one the allocating entry point
+(bitsort_ex) gives for the same keys, and that the calls leave the device's
+free memory unchanged.  Collected last on purpose.
 """
 import ctypes
 
@@ -14,6 +16,7 @@ import numpy as np
 import pytest
 
 import gen
+import oracle
 import paper_1312_0138_gb300 as bs
 
 pytestmark = pytest.mark.gpu
@@ -49,26 +52,56 @@ def _with_alloc(keys, max_value):
 
 
 @pytest.mark.parametrize("n,M", [(100_000, 1 << 20), (1 << 22, 1 << 26), (3, 40), (70_001, (1 << 31))])
-def test_noalloc_matches_allocating_entry_point_twice(n, M):
-    keys = _dev(gen.floyd(4242 + n, n, M))
+def test_noalloc_matches_oracle_and_allocating_entry_point_twice(n, M):
+    keys_np = gen.floyd(4242 + n, n, M)
+    keys = _dev(keys_np)
+    oracle_st, oracle_out = oracle.bitmap_sort(keys_np, M - 1)
     want_st, want_cnt, want = _with_alloc(keys, M - 1)
-    assert want_st == bs.OK
+    assert want_st == oracle_st == bs.OK
+    assert np.array_equal(want[:want_cnt], oracle_out)
     for _ in range(2):   # the shared scratch keeps the last call's contents
         st, cnt, got = _noalloc(keys, M - 1)
-        assert (st, cnt) == (want_st, want_cnt)
+        assert (st, cnt) == (oracle_st, oracle_out.size) == (want_st, want_cnt)
+        assert np.array_equal(got[:cnt], oracle_out)
         assert np.array_equal(got[:cnt], want[:want_cnt])
 
 
 def test_noalloc_error_semantics_match():
-    # duplicates and keys above max_value give the same outcome both ways
+    # duplicates and keys above max_value give the oracle's outcome, and the
+    # allocating entry point's, both ways
     for keys_np, mv in [(gen.uniform_with_replacement(7, 50_000, 1 << 16), (1 << 16) - 1),
                         (gen.floyd(8, 30_000, 1 << 20), (1 << 19) + 5)]:
         keys = _dev(keys_np)
         want = _with_alloc(keys, mv)
+        o_st, o_out = oracle.bitmap_sort(keys_np, mv)
+        assert want[:2] == (o_st, o_out.size)
         for _ in range(2):
             got = _noalloc(keys, mv)
             assert got[:2] == want[:2]
+            assert np.array_equal(got[2][: got[1]], o_out)
             assert np.array_equal(got[2][: got[1]], want[2][: want[1]])
+
+
+def test_noalloc_leaves_free_device_memory_unchanged():
+    import torch
+    keys_np = gen.floyd(99, 1 << 20, 1 << 26)
+    keys = _dev(keys_np)
+    out = torch.empty_like(keys)
+    res = torch.zeros(2, dtype=torch.int64, device="cuda")
+    lib = bs.load()
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.bitsort_noalloc(keys.data_ptr(), keys.numel(), (1 << 26) - 1, out.data_ptr(), res.data_ptr(), s) == bs.OK
+    torch.cuda.synchronize()   # the first call on a device finds its scratch array
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert lib.bitsort_noalloc(keys.data_ptr(), keys.numel(), (1 << 26) - 1, out.data_ptr(), res.data_ptr(),
+                                   s) == bs.OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    r = res.cpu().numpy()
+    assert int(r[0]) & 0xFFFFFFFF == bs.OK and int(r[1]) == keys_np.size
+    assert np.array_equal(_host(out), np.sort(keys_np))
 
 
 def test_noalloc_rejects_what_it_cannot_hold():
