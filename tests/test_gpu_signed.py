@@ -143,3 +143,11 @@ def test_signed_default_context_entry(ctx):
     st, cnt = bs.default_context(0).sync_status()
     assert st == bs.OK and cnt == keys.size
     assert np.array_equal(out.cpu().numpy(), np.sort(keys))
+
+
+def test_blocks_layout_signed_bias(ctx):
+    # the blocks-layout partition classifies x - min_value: signed keys
+    # straddling zero, over 2048 buckets, with refills of the blocks ahead
+    lo, hi = -(1 << 24), (1 << 24) - 1
+    keys = signed_keys(64, 1 << 23, lo, hi)
+    check(ctx, keys, lo, hi, path=bs.PATH_PARTITION, S=1 << 14, threads=512, layout=2)
