@@ -333,13 +333,7 @@ typedef enum {
  *   layout          PARTITION path: 0 = exact bucket ranges from a histogram
  *                   pass (n-entry buffer, the output buffer when it does not
  *                   alias the keys); 1 = fixed capacity min(slice, n) per
- *                   bucket in a context buffer, no histogram pass, every
- *                   partition tile reserving its run in each bucket; 2 =
- *                   blocks: as 1, but each partition CTA (one wave) takes
- *                   each bucket's entries in blocks of 64, one block ahead,
- *                   so no tile waits for a reservation; the capacity adds
- *                   two blocks per CTA (the unused entries get a value
- *                   outside the bucket, which its slice skips).
+ *                   bucket in a context buffer, no histogram pass.
  *   persistent      1: all phases in one persistent launch; 0: one kernel
  *                   per phase.
  *   emit            0 = the lanes walk the set bits of their bitmap words;
@@ -401,7 +395,7 @@ typedef struct {
     uint32_t bucket_threads;  /* block size of the bucket phase */
     uint32_t smem_bytes;      /* largest dynamic shared memory a launch of the plan asks for, per block */
     uint32_t reserved;
-    uint64_t scratch_bytes;   /* partition buffer of the capacity or blocks layout (0 for the exact layout) */
+    uint64_t scratch_bytes;   /* partition buffer of the capacity layout (0 for the other layouts) */
 } bitsort_plan_shape_t;
 
 /* The built-in plan rule for an array of n distinct keys bounded by

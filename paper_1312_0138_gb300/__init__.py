@@ -76,8 +76,8 @@ class Config(ctypes.Structure):
                 "summary": self.summary, "ms": self.ms}
 
 
-LAYOUT_EXACT, LAYOUT_CAPACITY, LAYOUT_BLOCKS = 0, 1, 2
-LAYOUT_NAMES = {0: "exact", 1: "capacity", 2: "blocks"}
+LAYOUT_EXACT, LAYOUT_CAPACITY = 0, 1
+LAYOUT_NAMES = {0: "exact", 1: "capacity"}
 EMIT_WORD, EMIT_RANK = 0, 1
 EMIT_NAMES = {0: "word", 1: "rank"}
 

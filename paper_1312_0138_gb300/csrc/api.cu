@@ -38,19 +38,7 @@ constexpr uint32_t kMaxSliceValues = 1u << 20;   // 128 KiB of bitmap per CTA
 // then skips the histogram pass for 16 GiB of scratch)
 constexpr uint64_t kCapacityScratchMax = 4ull << 30;
 inline uint64_t capacity_scratch_max(uint64_t n) { return n * 8 > kCapacityScratchMax ? n * 8 : kCapacityScratchMax; }
-// BLOCKS layout: the per-bucket capacity also holds the unused reserved
-// entries (at most two blocks per partition CTA), a few percent above the
-// CAPACITY bound for the arrays that take it
-inline uint64_t blocks_scratch_max(uint64_t n) { return n * 9 > kCapacityScratchMax ? n * 9 : kCapacityScratchMax; }
-// The BLOCKS partition runs one wave of CTAs; each ends holding about 1.5
-// blocks per bucket unused (the free tail of its current block and its
-// block ahead), written with values outside the bucket's range.  The layout
-// is taken where those entries stay below 1/24 of the keys.
-inline bool blocks_pays(uint64_t n, uint64_t nslices, uint64_t grid, uint64_t blk) {
-    return 3 * nslices * blk * grid * 24 <= 2 * n;
-}
-// shared memory of one SM (bytes) on GB300 and B200, for the one-wave grid
-constexpr uint32_t kSmemPerSM = 228u * 1024u;
+
 constexpr uint64_t kDefaultWaitNs = 4000ull * 1000ull * 1000ull;
 
 inline uint32_t round_up_u32(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
@@ -256,11 +244,6 @@ bsx_config bsx_default_config(int sms, uint64_t n, uint64_t M) {
     S = std::max(S, lo);
     S = std::min<uint64_t>(S, kMaxSliceValues);
     cfg.S = round_up_u32((uint32_t)S, 128);
-    // many buckets and many keys per bucket per partition CTA: blocks of
-    // reserved entries instead of a reservation per tile and bucket (one CTA
-    // per SM: the wide-fan-out partition runs at 1024 threads)
-    const uint64_t nb = ceil_div(M, cfg.S);
-    if (nb >= 1024 && blocks_pays(n, nb, (uint64_t)sms, kBlockEntries)) cfg.layout = LAYOUT_BLOCKS;
     return bsx_sanitize(cfg, n, M);
 }
 
@@ -280,9 +263,7 @@ bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
     if (cfg.wpl != 1 && cfg.wpl != 2 && cfg.wpl != 4 && cfg.wpl != 8) cfg.wpl = 2;
     if (cfg.stage && cfg.wpl == 2) cfg.wpl = 1;    // staged emission: 1, 4 or 8 words per lane
     if (!cfg.stage && cfg.wpl == 8) cfg.wpl = 4;   // direct emission: 1, 2 or 4
-    if (cfg.layout != LAYOUT_EXACT && cfg.layout != LAYOUT_CAPACITY && cfg.layout != LAYOUT_BLOCKS)
-        cfg.layout = LAYOUT_EXACT;
-    if (cfg.layout == LAYOUT_BLOCKS && (cfg.persistent || cfg.stream_part)) cfg.layout = LAYOUT_CAPACITY;
+    if (cfg.layout != LAYOUT_EXACT && cfg.layout != LAYOUT_CAPACITY) cfg.layout = LAYOUT_EXACT;
     if (cfg.path == BITSORT_PATH_FUSED && M > kMaxSliceValues) cfg.path = BITSORT_PATH_PARTITION;
     if (cfg.path == BITSORT_PATH_FUSED) {
         cfg.S = round_up_u32((uint32_t)M, 128);
@@ -295,12 +276,6 @@ bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
     S = std::min<uint64_t>(S, (M + 127) / 128 * 128);   // a slice never needs more than M values
     S = std::max<uint64_t>(S, 128);
     cfg.S = round_up_u32((uint32_t)S, 128);
-    if (cfg.path == BITSORT_PATH_PARTITION && cfg.layout == LAYOUT_BLOCKS) {
-        // (the exact grid is fixed by the plan; an upper bound of 2 CTAs per SM of 152 SMs here)
-        const uint64_t nb = ceil_div(M, cfg.S);
-        const uint64_t cap = std::min<uint64_t>(cfg.S, n) + 2ull * 304 * kBlockEntries;
-        if (nb < 2 || nb * cap * 4 > blocks_scratch_max(n)) cfg.layout = LAYOUT_CAPACITY;
-    }
     if (cfg.path == BITSORT_PATH_PARTITION && cfg.layout == LAYOUT_CAPACITY) {
         const uint64_t nb = ceil_div(M, cfg.S);
         const uint64_t cap = std::min<uint64_t>(cfg.S, n);
@@ -350,12 +325,11 @@ void bsx_describe(const bsx_config &cfg, const uint32_t *keys, uint32_t *out, ui
     a.stage = cfg.stage ? 1 : 0;
     a.phased = cfg.persistent ? 0 : 1;
     a.layout = cfg.path == BITSORT_PATH_PARTITION ? cfg.layout : LAYOUT_EXACT;
-    a.cap = a.layout != LAYOUT_EXACT ? std::min<uint64_t>(cfg.S, n) : 0;   // BLOCKS: the plan adds room for unused blocks
+    a.cap = a.layout == LAYOUT_CAPACITY ? std::min<uint64_t>(cfg.S, n) : 0;
     a.emit = cfg.emit;
     a.stage_cap = bsx_stage_cap(cfg, n, M);
     a.summary = (cfg.summary && cfg.path != BITSORT_PATH_GLOBAL) ? 1u : 0u;
     a.s_shift = (cfg.S & (cfg.S - 1)) == 0 ? (uint32_t)__builtin_ctz(cfg.S) : 0u;
-    a.blk = a.layout == LAYOUT_BLOCKS ? kBlockEntries : 0u;
     if (cfg.path == BITSORT_PATH_FUSED) {
         a.nslices = 1;
         a.key_tiles = 0;
@@ -480,7 +454,7 @@ static bsx_config fit_smem(uint32_t smem_optin, bsx_config cfg, uint64_t n, uint
 void bsx_plan_single(int sms, uint32_t smem_optin, const bsx_config &cfg0, uint64_t n, uint64_t M, bool in_place,
                      bool keys_aligned, bsx_single_plan &pl) {
     bsx_config cfg = fit_smem(smem_optin, bsx_sanitize(cfg0, n, M), n, M);
-    if (in_place && cfg.path == BITSORT_PATH_PARTITION && cfg.layout != LAYOUT_EXACT) cfg.layout = LAYOUT_EXACT;
+    if (in_place && cfg.path == BITSORT_PATH_PARTITION && cfg.layout == LAYOUT_CAPACITY) cfg.layout = LAYOUT_EXACT;
     ArrayDesc &a = pl.a;
     bsx_describe(cfg, nullptr, nullptr, n, M, a);
     const int T = cfg.threads;
@@ -489,9 +463,8 @@ void bsx_plan_single(int sms, uint32_t smem_optin, const bsx_config &cfg0, uint6
     int Tp = T, Tb = T;
     if (!cfg.persistent && T == 512 && partitioned) {
         const uint32_t wide = (uint32_t)(kKeysPerThread * 1024);
-        const uint32_t part_smem = a.layout == LAYOUT_BLOCKS ? part_blocks_smem_bytes(a.nslices, wide)
-                                   : pl.stream_part           ? part_stream_smem_bytes(a.nslices, wide)
-                                                              : part_smem_bytes(a.nslices, wide);
+        const uint32_t part_smem =
+            pl.stream_part ? part_stream_smem_bytes(a.nslices, wide) : part_phase_smem_bytes(a.nslices, wide);
         if (a.nslices >= 1024 && part_smem <= smem_optin) Tp = 1024;
         if (!cfg.stage && cfg.emit == EMIT_WORD && a.nslices >= 4u * (uint32_t)sms &&
             slice_smem_bytes(cfg.S, 1024, false) <= smem_optin)
@@ -501,39 +474,13 @@ void bsx_plan_single(int sms, uint32_t smem_optin, const bsx_config &cfg0, uint6
         a.tile_keys = (uint32_t)(kKeysPerThread * Tp);
         a.key_tiles = (uint32_t)ceil_div(n, (uint64_t)a.tile_keys);
     }
-    pl.part_grid = 0;
-    if (partitioned && a.layout == LAYOUT_BLOCKS) {
-        // one wave: as many CTAs as fit the SMs (registers cap a thread at 64)
-        const uint32_t smem = part_blocks_smem_bytes(a.nslices, a.tile_keys);
-        const uint32_t by_regs = 65536u / (64u * (uint32_t)Tp);
-        const uint32_t by_smem = kSmemPerSM / (smem + 1024u + (uint32_t)sizeof(uint64_t) * 64u);
-        const uint64_t per_sm = std::max<uint32_t>(1u, std::min(by_regs, by_smem));
-        const uint64_t grid = std::min<uint64_t>((uint64_t)sms * per_sm, a.key_tiles);
-        const uint64_t cap = (std::min<uint64_t>(cfg.S, n) + 2ull * grid * a.blk + a.blk - 1) / a.blk * a.blk;
-        const bool fits = smem <= smem_optin && (a.nslices + 1) <= 32u * (uint32_t)Tp &&
-                          (uint64_t)a.nslices * cap * 4 <= blocks_scratch_max(n) && cap < (1ull << 31);
-        if (fits) {
-            a.cap = cap;
-            pl.part_grid = (uint32_t)grid;
-        } else {
-            cfg.layout = LAYOUT_CAPACITY;   // the per-tile reservations instead
-            a.layout = LAYOUT_CAPACITY;
-            a.blk = 0;
-            if ((uint64_t)a.nslices * a.cap * 4 > capacity_scratch_max(n)) {
-                cfg.layout = LAYOUT_EXACT;
-                a.layout = LAYOUT_EXACT;
-                a.cap = 0;
-            }
-        }
-    }
     pl.cfg = cfg;
     pl.Tp = Tp;
     pl.Tb = Tb;
     pl.slice_smem = cfg.emit == EMIT_RANK ? rank_smem_bytes(cfg.S, a.stage_cap) : slice_smem_bytes(cfg.S, Tb, cfg.stage);
     pl.part_smem = !partitioned ? 0u
-                   : a.layout == LAYOUT_BLOCKS ? part_blocks_smem_bytes(a.nslices, a.tile_keys)
                    : pl.stream_part ? part_stream_smem_bytes(a.nslices, a.tile_keys)
-                                    : part_smem_bytes(a.nslices, a.tile_keys);
+                                    : part_phase_smem_bytes(a.nslices, a.tile_keys);
     pl.hist_smem = partitioned && a.layout == LAYOUT_EXACT ? hist_smem_bytes(a.nslices) : 0u;
     pl.engine_smem = cfg.persistent ? bsx_smem_for(cfg, a.nslices, a.tile_keys, a.stage_cap) : 0u;
 }
@@ -545,7 +492,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     const bool aligned = ((uintptr_t)keys & 15u) == 0;
     bsx_single_plan pl;
     bsx_plan_single(c->sms, c->smem_optin, cfg0, n, M, alias, aligned, pl);
-    if (pl.cfg.path == BITSORT_PATH_PARTITION && (pl.a.layout == LAYOUT_CAPACITY || pl.a.layout == LAYOUT_BLOCKS)) {
+    if (pl.cfg.path == BITSORT_PATH_PARTITION && pl.a.layout == LAYOUT_CAPACITY) {
         const uint64_t entries = (uint64_t)pl.a.nslices * pl.a.cap;
         bitsort_status_t st = bsx_ensure_part(c, entries, stream);
         if (st == BITSORT_ERR_NOMEM && entries * 4 > kCapacityScratchMax) {
@@ -568,7 +515,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     a.out = out;
     a.stall = stall;
     a.bias = bias;
-    if (cfg.path == BITSORT_PATH_PARTITION && (a.layout == LAYOUT_CAPACITY || a.layout == LAYOUT_BLOCKS)) {
+    if (cfg.path == BITSORT_PATH_PARTITION && a.layout == LAYOUT_CAPACITY) {
         a.part = c->part;
     } else if (cfg.path == BITSORT_PATH_PARTITION) {
         if (alias) {
@@ -623,9 +570,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     const int Tp = pl.Tp, Tb = pl.Tb;
     int launched = 0;
     auto phase = [&](int kind, uint32_t items, uint32_t smem) -> bool {
-        const int Tk = (kind == IT_HIST || kind == IT_PART || kind == IT_PARTS || kind == IT_PARTB) ? Tp
-                       : kind == IT_BUCKET                                                          ? Tb
-                                                                                                    : T;
+        const int Tk = (kind == IT_HIST || kind == IT_PART || kind == IT_PARTS) ? Tp : kind == IT_BUCKET ? Tb : T;
         if (items == 0) return true;
         if (smem > c->smem_optin) {
             bsx_note_error((int)cudaErrorInvalidValue, "shared memory above the per-block limit");
@@ -639,11 +584,10 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         }
         int per_sm = 1;
         if (kernel_max_blocks_per_sm(kind, Tk, smem, &per_sm) != 0 || per_sm < 1) per_sm = 1;
-        // slice phases and the streaming HIST / GSCATTER / PARTS / PARTB
+        // slice phases and the streaming HIST / GSCATTER / PARTS
         // phases: one wave of resident CTAs; PART: a few tiles per CTA
         const bool one_wave = kind != IT_PART;
         uint64_t grid = (uint64_t)c->sms * (uint64_t)per_sm * (one_wave ? 1u : 8u);
-        if (kind == IT_PARTB && grid > pl.part_grid) grid = pl.part_grid;   // the capacity is sized for it
         if (grid > items) grid = items;
         int e = kernel_launch(kind, q, Tk, smem, (int)grid, stream, launched > 0);
         if (e != 0) {
@@ -663,7 +607,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         ok = phase(IT_BUCKET, 1, sl);
     } else if (a.path == BITSORT_PATH_PARTITION) {
         // tiles of 16-byte aligned keys may stream through bulk copies
-        const int pk = a.layout == LAYOUT_BLOCKS ? (int)IT_PARTB : pl.stream_part ? (int)IT_PARTS : (int)IT_PART;
+        const int pk = pl.stream_part ? (int)IT_PARTS : (int)IT_PART;
         if (a.layout == LAYOUT_EXACT) ok = phase(IT_HIST, a.key_tiles, pl.hist_smem);
         ok = ok && phase(pk, a.key_tiles, pl.part_smem) && phase(IT_BUCKET, a.nslices, sl);
     } else {
@@ -912,7 +856,7 @@ extern "C" bitsort_status_t bitsort_plan_rule(int sms, uint32_t smem_per_block, 
         shape->bucket_threads = (uint32_t)pl.Tb;
         shape->smem_bytes = pl.cfg.persistent ? pl.engine_smem
                                               : std::max(pl.slice_smem, std::max(pl.part_smem, pl.hist_smem));
-        shape->scratch_bytes = pl.a.layout != LAYOUT_EXACT ? (uint64_t)pl.a.nslices * pl.a.cap * 4u : 0u;
+        shape->scratch_bytes = pl.a.layout == LAYOUT_CAPACITY ? (uint64_t)pl.a.nslices * pl.a.cap * 4u : 0u;
     }
     return BITSORT_OK;
 }
@@ -954,7 +898,7 @@ std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_
     for (int threads : {256, 512}) {
         for (uint32_t wpl : {1u, 2u, 4u}) {
             if (M <= kMaxSliceValues) push(BITSORT_PATH_FUSED, M, threads, wpl, false, LAYOUT_EXACT);
-            for (uint32_t layout : {(uint32_t)LAYOUT_EXACT, (uint32_t)LAYOUT_CAPACITY, (uint32_t)LAYOUT_BLOCKS}) {
+            for (uint32_t layout : {(uint32_t)LAYOUT_EXACT, (uint32_t)LAYOUT_CAPACITY}) {
                 for (int k : {1, 2, 3, 4, 6, 8})
                     push(BITSORT_PATH_PARTITION, ceil_div(M, (uint64_t)k * c->sms), threads, wpl, false, layout);
                 for (int lg : {16, 18, 20}) push(BITSORT_PATH_PARTITION, 1ull << lg, threads, wpl, false, layout);
@@ -980,7 +924,6 @@ std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_
         }
         push(BITSORT_PATH_PARTITION, ceil_div(M, 2ull * c->sms), threads, 1, true, LAYOUT_CAPACITY);
         push(BITSORT_PATH_PARTITION, ceil_div(M, 2ull * c->sms), threads, 1, true, LAYOUT_EXACT);
-        push(BITSORT_PATH_PARTITION, ceil_div(M, 2ull * c->sms), threads, 1, true, LAYOUT_BLOCKS);
     }
     // shared memory must fit
     std::vector<bsx_config> fit;

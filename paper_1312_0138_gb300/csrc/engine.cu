@@ -633,11 +633,9 @@ __device__ void complete_slices(const ArrayDesc &a, SharedMisc &m, uint32_t coun
             }
         }
         __syncthreads();
-        const bool blocks = a.layout == LAYOUT_BLOCKS;
         for (uint32_t i = threadIdx.x; i < a.nslices; i += T) {
             a.look[i] = 0;
             a.cursor[i] = 0;
-            if (blocks) a.counts[i] = 0;
         }
     } else {
         if (a.nslices > 1) total = ld_acquire_u64(&a.look[a.nslices - 1]) & LB_VALUE;
@@ -916,27 +914,25 @@ __device__ void item_part(const EngineParams &P, const ArrayDesc &a, uint32_t ti
     }
 }
 
-// ------------------------------------------ PART, BLOCKS layout (one wave)
-// A CTA of the one-wave BLOCKS partition kernel takes tiles t, t + G, ... and
-// keeps per bucket, in shared memory, its next free entry `cur` (inside the
-// current block: the entries up to the next multiple of blk are free) and one
-// reserved block ahead `nxt`.  A tile's run for a bucket goes to the free tail
-// of the current block and, past it, to the block ahead (two pieces at most);
-// the bucket then gets a new block ahead at the start of the CTA's next tile,
-// so no tile waits for a global atomic except when one bucket brings more
-// keys than the tail and a whole block (then a run of whole blocks is
-// reserved at once).  Exact key counts per bucket go to counts[b] (reductions
-// that nothing waits for).  Every reservation is a multiple of blk and
-// starts at a multiple of blk, so a CTA never holds more than 2*blk unused
-// entries of a bucket: with cap = min(S, n) + 2*G*blk distinct keys never
-// overflow.  A bucket that does overflow (repeated keys) stops being written
-// (cur = cap); its bucket item reads the whole input instead.
-constexpr uint32_t kNoBlock = 0xFFFFFFFFu;
-
-__device__ __forceinline__ uint32_t reserve_block(uint32_t *cursor, uint32_t blk, uint32_t cap) {
-    const uint32_t at = atomicAdd(cursor, blk);
-    return at <= cap - blk ? at : kNoBlock;
-}
+// ------------------------------------------------- PART, phase kernel
+// The partition phase of a single sort (the persistent engine and the
+// streaming partition use item_part / part_stream above).  A CTA takes tiles
+// t, t + G, ...; per tile:
+//   1. every key's bin and its rank among the tile's keys of that bin come
+//      from one shared-memory atomic;
+//   2. each thread owns a contiguous range of bins: it issues the global
+//      reservations of its bins' runs (an atomic on the bucket's cursor) at
+//      once, and uses their results only in the second pass of the scan, so
+//      that their round trip overlaps the scan's first pass and barriers;
+//   3. that second pass writes the tile-local prefix of every bin and its run
+//      words {start - prefix, fit + prefix};
+//   4. the tile is reordered by bin in shared memory, and each bin's keys
+//      leave in consecutive stores; the writer recomputes a key's bin from
+//      the key instead of reading a tag array (ALU instead of two
+//      shared-memory accesses per key).
+// `base` (per bin, filled once per CTA) is where the bucket's range starts:
+// its histogram offset (EXACT) or b * cap (CAPACITY).  Positions are 32-bit
+// (the buffer has at most 2^32 entries).
 
 // Bin of a key for the partition: value y = x - bias; with kCheck, keys above
 // max_value go to the discard bin nb.  kShift: S = 2^sh.
@@ -949,23 +945,41 @@ __device__ __forceinline__ uint32_t part_bin(uint32_t x, uint32_t bias, uint32_t
     return b;
 }
 
+constexpr int kOwnEarly = 4;   // bins per thread whose reservations are issued ahead of the scan
+
+// Run words of bin i from its count c, tile prefix p and reservation `at`.
+__device__ __forceinline__ uint2 part_run(const ArrayDesc &a, uint32_t i, uint32_t c, uint32_t p, uint32_t at,
+                                          uint32_t base, bool capacity) {
+    uint32_t fit;
+    if (capacity) {
+        const uint64_t cap = a.cap;
+        fit = at >= cap ? 0u : (uint32_t)min((uint64_t)c, cap - at);
+        if (fit < c) atomicOr(&a.sync[SY_OVERFLOW], 1u);   // only with repeated keys
+    } else {
+        const uint64_t st = (uint64_t)base + at;
+        fit = st >= a.n ? 0u : (uint32_t)min((uint64_t)c, a.n - st);   // a sane scratch never clips
+    }
+    return make_uint2(base + at - p, fit + p);
+}
+
 // One tile: x[j] holds tile element j*T + threadIdx.x (valid while below
-// nkeys; every element when kFull).  The thread owns bins [lo_bin, hi_bin)
-// for the scan and the run assignment, and zeroes them again at the end, so
+// nkeys; every element when kFull).  The thread owns buckets [lo_bin,
+// hi_bin) (the discard bin nb, keys above max_value, comes after all of
+// them and is never written); it zeroes their counts again at the end, so
 // that the next tile starts with an empty histogram.  Ends with a barrier.
 template <int T, bool kShift, bool kCheck, bool kFull>
-__device__ void part_blocks_tile(const ArrayDesc &a, const uint32_t (&x)[kKeysPerThread], uint32_t nkeys,
-                                 uint32_t *hist, uint4 *binfo, uint32_t *cur, uint32_t *nxt, uint32_t *sorted,
-                                 uint32_t lo_bin, uint32_t hi_bin, uint32_t &refill, SharedMisc &m) {
+__device__ void part_tile_phase(const ArrayDesc &a, const uint32_t (&x)[kKeysPerThread], uint32_t nkeys,
+                                uint32_t *hist, const uint32_t *base, uint2 *run, uint32_t *sorted, uint32_t lo_bin,
+                                uint32_t hi_bin, SharedMisc &m) {
     constexpr int K = kKeysPerThread;
     constexpr int NW = T / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nb = a.nslices;
     const uint32_t bias = a.bias, maxv = (uint32_t)(a.M - 1), sh = a.s_shift;
     const uint64_t magic = a.div_magic;
-    const uint32_t cap = (uint32_t)a.cap, blk = a.blk, bmask = blk - 1;
+    const bool capacity = a.layout == LAYOUT_CAPACITY;
 
-    // ranks inside the tile (bin << 16 | rank)
+    // 1. ranks inside the tile (bin << 16 | rank)
     uint32_t br[K];
     bool bad = false;
 #pragma unroll
@@ -977,17 +991,28 @@ __device__ void part_blocks_tile(const ArrayDesc &a, const uint32_t (&x)[kKeysPe
             br[j] = (b << 16) | atomicAdd(&hist[b], 1u);
         }
     }
-    if (kCheck) {
+    if (kCheck && capacity) {
         bad = __syncthreads_or(bad);
         if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
     } else {
-        __syncthreads();
+        __syncthreads();   // (EXACT: the histogram pass reports keys above max_value)
     }
 
-    // exclusive scan of the counts over the threads' contiguous bin ranges;
-    // in the same pass every bucket with keys gets its run
+    // 2. reservations of this thread's buckets, issued before the scan
+    const bool early = hi_bin - lo_bin <= (uint32_t)kOwnEarly;
+    uint32_t at[kOwnEarly];
     uint32_t own = 0;
-    for (uint32_t i = lo_bin; i < hi_bin; ++i) own += hist[i];
+    if (early) {
+#pragma unroll
+        for (int k = 0; k < kOwnEarly; ++k) {
+            const uint32_t i = lo_bin + k;
+            const uint32_t c = i < hi_bin ? hist[i] : 0u;
+            at[k] = c ? atomicAdd(&a.cursor[i], c) : 0u;
+            own += c;
+        }
+    } else {
+        for (uint32_t i = lo_bin; i < hi_bin; ++i) own += hist[i];
+    }
     const uint32_t incl = warp_incl_scan_u32(own, lane);
     if (lane == 31) m.wcount[warp] = incl;
     __syncthreads();
@@ -995,101 +1020,77 @@ __device__ void part_blocks_tile(const ArrayDesc &a, const uint32_t (&x)[kKeysPe
         const uint32_t w = lane < NW ? m.wcount[lane] : 0u;
         const uint32_t wi = warp_incl_scan_u32(w, lane);
         if (lane < NW) m.wbase[lane] = wi - w;
-    }
-    __syncthreads();
-    uint32_t run = m.wbase[warp] + incl - own;
-    for (uint32_t i = lo_bin; i < hi_bin; ++i) {
-        const uint32_t c = hist[i];
-        const uint32_t p = run;
-        run += c;
-        hist[i] = p;
-        if (c == 0 || i >= nb) continue;   // (the discard bin's run words are fixed: never stored)
-        const uint32_t cu = cur[i];
-        uint32_t A = cu, B = 0u, split = c;
-        if (cu >= cap) {
-            A = B = cap;   // overflowed bucket: nothing more is stored
-            split = 0u;
-        } else {
-            const uint32_t left = (0u - cu) & bmask;
-            if (c <= left) {
-                cur[i] = cu + c;
-            } else {
-                const uint32_t q = c - left;
-                const uint32_t nx = nxt[i];
-                split = left;
-                if (q <= blk && nx != kNoBlock) {
-                    B = nx;
-                    cur[i] = nx + q;
-                    nxt[i] = kNoBlock;
-                    refill |= 1u << (i - lo_bin);
-                } else {
-                    const uint32_t want = (q + bmask) & ~bmask;
-                    const uint32_t at = atomicAdd(&a.cursor[i], want);
-                    B = at;
-                    cur[i] = at + q;
-                    if (at > cap - want) {   // past the bucket's capacity (repeated keys)
-                        atomicOr(&a.sync[SY_OVERFLOW], 1u);
-                        cur[i] = cap;
-                    }
-                }
-            }
+        if (kCheck && lane == 31) {   // the discard bin after every bucket
+            if (hist[nb]) run[nb] = make_uint2(0u, 0u);
+            hist[nb] = wi;
         }
-        binfo[i] = make_uint4(A - p, B - split - p, split + p, 0u);
-        atomicAdd(&a.counts[i], c);
     }
     __syncthreads();
 
-    // reorder the tile by bin
+    // 3. tile prefix and run words of every bucket with keys
+    uint32_t p = m.wbase[warp] + incl - own;
+    if (early) {
+#pragma unroll
+        for (int k = 0; k < kOwnEarly; ++k) {
+            const uint32_t i = lo_bin + k;
+            if (i < hi_bin) {
+                const uint32_t c = hist[i];
+                hist[i] = p;
+                if (c) run[i] = part_run(a, i, c, p, at[k], base[i], capacity);
+                p += c;
+            }
+        }
+    } else {
+        for (uint32_t i = lo_bin; i < hi_bin; ++i) {
+            const uint32_t c = hist[i];
+            hist[i] = p;
+            if (c) run[i] = part_run(a, i, c, p, atomicAdd(&a.cursor[i], c), base[i], capacity);
+            p += c;
+        }
+    }
+    __syncthreads();
+
+    // 4. reorder by bin, then each bin's keys leave in consecutive stores
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         if (kFull || br[j] != 0xFFFFFFFFu) sorted[hist[br[j] >> 16] + (br[j] & 0xFFFFu)] = x[j];
     }
     __syncthreads();
-
-    // each bin's keys leave in consecutive stores (the bin is recomputed from
-    // the key); the histogram is zeroed for the next tile
     uint32_t *part = a.part;
 #pragma unroll 4
     for (int j = 0; j < K; ++j) {
         const uint32_t i = (uint32_t)j * T + threadIdx.x;
         if (kFull || i < nkeys) {
             const uint32_t v = sorted[i];
-            const uint32_t b = part_bin<kShift, kCheck>(v, bias, maxv, sh, magic, nb);
-            const uint4 f = binfo[b];
-            const uint32_t rel = (i < f.z ? f.x : f.y) + i;
-            if (rel < cap) part[(uint64_t)b * cap + rel] = v;
+            const uint2 f = run[part_bin<kShift, kCheck>(v, bias, maxv, sh, magic, nb)];
+            if (i < f.y) part[f.x + i] = v;
         }
     }
     for (uint32_t i = lo_bin; i < hi_bin; ++i) hist[i] = 0u;
+    if (kCheck && threadIdx.x == 0) hist[nb] = 0u;
     __syncthreads();
 }
 
 template <int T>
-__device__ void part_blocks(const EngineParams &P, const ArrayDesc &a, char *smem, SharedMisc &m) {
+__device__ void part_phase(const EngineParams &P, const ArrayDesc &a, char *smem, SharedMisc &m) {
     constexpr int K = kKeysPerThread;
     const uint32_t nb = a.nslices, nbins = nb + 1;
-    const uint32_t cap = (uint32_t)a.cap, blk = a.blk, bmask = blk - 1;
-    // layout (as part_blocks_smem_bytes): counts / prefixes | run words | cur | nxt | tile
+    // layout (as part_phase_smem_bytes): counts / prefixes | bucket bases | run words | tile
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
-    uint4 *binfo = reinterpret_cast<uint4 *>(smem + ((nbins * 4u + 15u) & ~15u));
-    uint32_t *cur = reinterpret_cast<uint32_t *>(binfo + nbins);
-    uint32_t *nxt = cur + nb;
-    uint32_t *sorted = nxt + nb;
-    const uint32_t per = (nbins + T - 1) / T;
-    const uint32_t lo_bin = min(nbins, threadIdx.x * per), hi_bin = min(nbins, lo_bin + per);
+    uint32_t *base = hist + nbins;
+    uint2 *run = reinterpret_cast<uint2 *>(smem + ((nbins * 8u + 7u) & ~7u));
+    uint32_t *sorted = reinterpret_cast<uint32_t *>(run + nbins);
+    const uint32_t per = (nb + T - 1) / T;
+    const uint32_t lo_bin = min(nb, threadIdx.x * per), hi_bin = min(nb, lo_bin + per);
+    const bool capacity = a.layout == LAYOUT_CAPACITY;
     for (uint32_t i = lo_bin; i < hi_bin; ++i) {
         hist[i] = 0u;
-        if (i < nb) {
-            cur[i] = 0u;   // no current block (no free tail)
-            nxt[i] = reserve_block(&a.cursor[i], blk, cap);
-        } else {
-            binfo[i] = make_uint4(cap, cap, 0u, 0u);   // discard bin: every position at or past cap
-        }
+        base[i] = capacity ? (uint32_t)((uint64_t)i * a.cap) : (uint32_t)__ldcg(&a.offsets[i]);
     }
+    if (threadIdx.x == 0) hist[nb] = 0u;
     __syncthreads();
     const bool shift = a.s_shift != 0;
     const bool check = a.M != (1ull << 32);
-    uint32_t refill = 0;
     for (uint32_t t = blockIdx.x; t < a.key_tiles; t += gridDim.x) {
         const uint64_t lo = (uint64_t)t * a.tile_keys;
         const uint32_t nkeys = (uint32_t)(min(lo + a.tile_keys, a.n) - lo);
@@ -1109,42 +1110,11 @@ __device__ void part_blocks(const EngineParams &P, const ArrayDesc &a, char *sme
                 x[j] = e < nkeys ? __ldcs(a.keys + lo + e) : 0u;
             }
         }
-        // the blocks ahead this thread's buckets used up in the previous tile
-        for (uint32_t f = refill; f; f &= f - 1u) {
-            const uint32_t i = lo_bin + (uint32_t)(__ffs(f) - 1);
-            nxt[i] = reserve_block(&a.cursor[i], blk, cap);
-        }
-        refill = 0;
-        if (!full) {
-            part_blocks_tile<T, false, true, false>(a, x, nkeys, hist, binfo, cur, nxt, sorted, lo_bin, hi_bin,
-                                                    refill, m);
-        } else if (shift && check) {
-            part_blocks_tile<T, true, true, true>(a, x, nkeys, hist, binfo, cur, nxt, sorted, lo_bin, hi_bin, refill, m);
-        } else if (shift) {
-            part_blocks_tile<T, true, false, true>(a, x, nkeys, hist, binfo, cur, nxt, sorted, lo_bin, hi_bin, refill,
-                                                   m);
-        } else if (check) {
-            part_blocks_tile<T, false, true, true>(a, x, nkeys, hist, binfo, cur, nxt, sorted, lo_bin, hi_bin, refill,
-                                                   m);
-        } else {
-            part_blocks_tile<T, false, false, true>(a, x, nkeys, hist, binfo, cur, nxt, sorted, lo_bin, hi_bin,
-                                                    refill, m);
-        }
-    }
-    // the entries this CTA reserved and left unused get a value outside their
-    // bucket's range (bucket i starts at value i*S + bias: the sentinel is
-    // one below it, modulo 2^32), which the bucket item skips
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t i = warp; i < nb; i += T / 32) {
-        const uint32_t cu = cur[i], nx = nxt[i];
-        const uint32_t sentinel = (uint32_t)((uint64_t)i * a.S) + a.bias - 1u;
-        uint32_t *reg = a.part + (uint64_t)i * cap;
-        if (cu < cap) {
-            const uint32_t left = (0u - cu) & bmask;
-            for (uint32_t k = lane; k < left; k += 32) reg[cu + k] = sentinel;
-        }
-        if (nx != kNoBlock)
-            for (uint32_t k = lane; k < blk; k += 32) reg[nx + k] = sentinel;
+        if (!full) part_tile_phase<T, false, true, false>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
+        else if (shift && check) part_tile_phase<T, true, true, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
+        else if (shift) part_tile_phase<T, true, false, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
+        else if (check) part_tile_phase<T, false, true, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
+        else part_tile_phase<T, false, false, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
     }
 }
 
@@ -1385,10 +1355,7 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     const uint32_t *src = a.keys;
     uint64_t lo = 0, hi = a.n;
     bool filter_range = !partitioned;   // input keys above max_value are skipped and reported
-    const bool blocks = a.layout == LAYOUT_BLOCKS;
-    if (partitioned && (a.layout == LAYOUT_CAPACITY || blocks)) {
-        // the bucket's region: its keys (BLOCKS: and reserved entries left
-        // unused, which hold a value outside the slice)
+    if (partitioned && a.layout == LAYOUT_CAPACITY) {
         const uint64_t filled = __ldcg(&a.cursor[b]);
         if (filled <= a.cap) {
             src = a.part;
@@ -1396,12 +1363,11 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
             hi = lo + filled;
         }
         if (known_offsets(a)) {   // the slice starts after the keys of the buckets before it
-            const uint32_t *keys_per_bucket = blocks ? a.counts : a.cursor;
             uint64_t before = 0;
-            for (uint32_t i = threadIdx.x; i < b; i += T) before += __ldcg(&keys_per_bucket[i]);
+            for (uint32_t i = threadIdx.x; i < b; i += T) before += __ldcg(&a.cursor[i]);
             before = warp_sum_u64(before);
             if ((threadIdx.x & 31) == 0) m.wsum[threadIdx.x >> 5] = before;
-            if (threadIdx.x == 0) m.expect = blocks ? __ldcg(&a.counts[b]) : filled;
+            if (threadIdx.x == 0) m.expect = filled;
         }
     } else if (partitioned) {
         src = a.part;
@@ -1425,7 +1391,7 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     __syncthreads();
     if (threadIdx.x == 0) {
         m.summ_clean = 1u;
-        if (partitioned && (a.layout == LAYOUT_CAPACITY || blocks) && known_offsets(a)) {
+        if (partitioned && a.layout == LAYOUT_CAPACITY && known_offsets(a)) {
             uint64_t before = 0;
             for (int w = 0; w < NW; ++w) before += m.wsum[w];
             m.known = before;
@@ -1471,7 +1437,7 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
     bad = __syncthreads_or(bad);
     if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
     if (partitioned && threadIdx.x == 0) {
-        if (!blocks) a.counts[b] = 0;          // (BLOCKS: later slices still read it; the last CTA clears it)
+        a.counts[b] = 0;
         if (a.nslices == 1) a.cursor[b] = 0;   // else the last CTA clears the cursors (known offsets)
     }
     if (sparse) {
@@ -1715,14 +1681,9 @@ __global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constan
     } else if constexpr (TYPE == IT_PARTS) {
         part_stream<T>(P, a, smem, m);
         pdl_trigger();
-    } else if constexpr (TYPE == IT_PARTB) {
-        part_blocks<T>(P, a, smem, m);
-        pdl_trigger();
+
     } else if constexpr (TYPE == IT_PART) {
-        for (uint32_t t = blockIdx.x; t < P.total_items; t += gridDim.x) {
-            item_part<T>(P, a, t, smem, m);
-            __syncthreads();
-        }
+        part_phase<T>(P, a, smem, m);
         pdl_trigger();
     } else {
         // HIST / GSCATTER stream one contiguous chunk of keys per CTA (one
@@ -1750,7 +1711,6 @@ static KernelFn kernel_for(int kind, int threads) {
             case IT_GSCATTER: return phase_kernel<256, IT_GSCATTER>;
             case IT_GSCAN: return phase_kernel<256, IT_GSCAN>;
             case IT_PARTS: return phase_kernel<256, IT_PARTS>;
-            case IT_PARTB: return phase_kernel<256, IT_PARTB>;
         }
     } else if (threads == 512) {
         switch (kind) {
@@ -1761,7 +1721,6 @@ static KernelFn kernel_for(int kind, int threads) {
             case IT_GSCATTER: return phase_kernel<512, IT_GSCATTER>;
             case IT_GSCAN: return phase_kernel<512, IT_GSCAN>;
             case IT_PARTS: return phase_kernel<512, IT_PARTS>;
-            case IT_PARTB: return phase_kernel<512, IT_PARTB>;
         }
     } else if (threads == 1024) {
         // one CTA per SM for the phase kernels of a single sort (the
@@ -1773,15 +1732,13 @@ static KernelFn kernel_for(int kind, int threads) {
             case IT_GSCATTER: return phase_kernel<1024, IT_GSCATTER>;
             case IT_GSCAN: return phase_kernel<1024, IT_GSCAN>;
             case IT_PARTS: return phase_kernel<1024, IT_PARTS>;
-            case IT_PARTB: return phase_kernel<1024, IT_PARTB>;
         }
     }
     return nullptr;
 }
 
 int engine_set_smem_limit(int threads, uint32_t smem_bytes) {
-    for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN, (int)IT_PARTS,
-                     (int)IT_PARTB}) {
+    for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN, (int)IT_PARTS}) {
         if (kind == -1 && threads == 1024) continue;   // no persistent engine at 1024 threads
         KernelFn f = kernel_for(kind, threads);
         if (!f) return (int)cudaErrorInvalidValue;

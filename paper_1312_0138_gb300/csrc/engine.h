@@ -33,8 +33,7 @@
 namespace bsx {
 
 enum ItemType : uint32_t { IT_HIST = 0, IT_PART = 1, IT_BUCKET = 2, IT_GSCATTER = 3, IT_GSCAN = 4,
-                           IT_PARTS = 5 /* PART tiles streamed through bulk copies (phase kernel only) */,
-                           IT_PARTB = 6 /* PART tiles of the BLOCKS layout (phase kernel only, one wave) */ };
+                           IT_PARTS = 5 /* PART tiles streamed through bulk copies (phase kernel only) */ };
 
 enum SyncSlot : uint32_t {
     SY_HIST_DONE = 0,     // HIST tiles finished
@@ -83,7 +82,7 @@ struct __align__(16) ArrayDesc {
     uint32_t stage_cap;         // EMIT_RANK: outputs a slice may stage in shared memory
     uint32_t summary;           // 1: sparse slices keep a summary bitmap (one bit per word)
     uint32_t bias;              // keys are classified as x - bias (mod 2^32); outputs get it back
-    uint32_t blk;               // BLOCKS layout: entries per reserved block (a power of 2)
+    uint32_t pad_;
     uint32_t s_shift;           // log2(S) when S is a power of 2 (bucket = shift), else 0 (division)
 };
 
@@ -106,16 +105,7 @@ enum Emit : uint32_t { EMIT_WORD = 0, EMIT_RANK = 1 };
 //   CAPACITY  bucket b owns entries [b*cap, (b+1)*cap) with cap = min(S, n):
 //             distinct keys never overflow it, so no histogram pass is needed.
 //             Every tile reserves its run in each bucket with a global atomic.
-//   BLOCKS    as CAPACITY, but the entries of bucket b are handed out in
-//             blocks of `blk` entries, and a CTA of the (one-wave) partition
-//             kernel keeps a current block and one block ahead per bucket in
-//             shared memory: its tiles reserve nothing on their critical path
-//             (a new block ahead is reserved at the start of the next tile).
-//             Entries a CTA reserved and left unused get a value outside the
-//             bucket's range, which the bucket item skips; counts[b] receives
-//             the bucket's exact key count.  cap = min(S, n) + 2*G*blk for G
-//             partition CTAs, so distinct keys never overflow it.
-enum Layout : uint32_t { LAYOUT_EXACT = 0, LAYOUT_CAPACITY = 1, LAYOUT_BLOCKS = 2 };
+enum Layout : uint32_t { LAYOUT_EXACT = 0, LAYOUT_CAPACITY = 1 };
 
 // A run of `count` consecutive tickets that all belong to one (array, type).
 struct Segment {
@@ -165,12 +155,11 @@ inline uint32_t part_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
     return (nslices + 1) * 12u + tile_keys * 6u + 16u;
 }
 inline uint32_t hist_smem_bytes(uint32_t nslices) { return nslices * 4u; }
-// BLOCKS-layout PART: per bin the tile count / prefix and the run words
-// (16 bytes), per bucket the CTA's current position and block ahead; the tile
-inline uint32_t part_blocks_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
-    return (nslices + 1) * 4u + ((nslices + 1) * 16u + 15u) / 16u * 16u + nslices * 8u + tile_keys * 4u + 32u;
+// PART phase kernel: per bin (plus the discard bin) count / prefix, bucket
+// base and run words; the tile
+inline uint32_t part_phase_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
+    return (((nslices + 1) * 8u + 7u) & ~7u) + (nslices + 1) * 8u + tile_keys * 4u + 16u;
 }
-constexpr uint32_t kBlockEntries = 64;   // default entries per reserved block (BLOCKS layout)
 // streaming PART: bins, bucket tags, two landing buffers, two mbarriers (128-byte aligned parts)
 inline uint32_t part_stream_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
     const uint32_t a = ((nslices + 1) * 12u + 127u) & ~127u;

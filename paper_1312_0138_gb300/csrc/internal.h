@@ -125,7 +125,6 @@ struct bsx_single_plan {
     bool stream_part = false;         // the partition streams its tiles through bulk copies
     uint32_t slice_smem = 0, part_smem = 0, hist_smem = 0;   // dynamic shared memory per phase (bytes)
     uint32_t engine_smem = 0;         // persistent plan: of the one launch
-    uint32_t part_grid = 0;           // BLOCKS layout: CTAs of the one-wave partition (0: the launcher's choice)
 };
 void bsx_plan_single(int sms, uint32_t smem_optin, const bsx_config &cfg0, uint64_t n, uint64_t M, bool in_place,
                      bool keys_aligned, bsx_single_plan &pl);

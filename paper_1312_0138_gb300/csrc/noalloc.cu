@@ -129,7 +129,7 @@ extern "C" bitsort_status_t bitsort_noalloc(const uint32_t *keys, uint64_t n, ui
     struct Phase { int kind; uint32_t items; uint32_t smem; };
     const Phase phases[3] = {
         {IT_HIST, a.key_tiles, hist_smem_bytes(a.nslices)},
-        {IT_PART, a.key_tiles, part_smem_bytes(a.nslices, a.tile_keys)},
+        {IT_PART, a.key_tiles, part_phase_smem_bytes(a.nslices, a.tile_keys)},
         {IT_BUCKET, a.nslices, slice_smem_bytes(cfg.S, kThreads, false)},
     };
     for (int i = 0; i < 3; ++i) {

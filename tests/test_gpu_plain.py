@@ -70,12 +70,11 @@ CONFIGS = [
     ("global_S16K_w1", bs.PATH_GLOBAL, 1 << 14, 512, dict(words_per_lane=1)),
     ("global_S1M_256_w4", bs.PATH_GLOBAL, 1 << 20, 256, dict(words_per_lane=4)),
     ("global_S64K_persist_stage", bs.PATH_GLOBAL, 1 << 16, 256, dict(persistent=1, stage=1)),
-    # blocks layout: one-wave partition taking each bucket's entries in blocks
-    ("blocks_S4096", bs.PATH_PARTITION, 4096, 512, dict(layout=2)),
-    ("blocks_S64K_stage", bs.PATH_PARTITION, 1 << 16, 512, dict(layout=2, stage=1)),
-    ("blocks_S1M_w2", bs.PATH_PARTITION, 1 << 20, 512, dict(layout=2, words_per_lane=2)),
-    ("blocks_odd_256", bs.PATH_PARTITION, 300_032, 256, dict(layout=2)),
-    ("blocks_odd_1024", bs.PATH_PARTITION, 883_072, 1024, dict(layout=2)),
+    # partition tiles with a power-of-two slice (bucket by shift) and with any slice
+    ("cap_S4096_pow2", bs.PATH_PARTITION, 4096, 512, dict(layout=1)),
+    ("exact_S1M_w2_pow2", bs.PATH_PARTITION, 1 << 20, 512, dict(layout=0, words_per_lane=2)),
+    ("cap_odd_256", bs.PATH_PARTITION, 300_032, 256, dict(layout=1)),
+    ("cap_odd_1024", bs.PATH_PARTITION, 883_072, 1024, dict(layout=1)),
 ]
 
 
@@ -99,7 +98,6 @@ STRATS = [
     ("rank_fused", dict(path=bs.PATH_FUSED, emit=1)),
     ("runs8", dict(path=bs.PATH_PARTITION, S=4096, layout=1, stage=1, words_per_lane=8)),
     ("stream", dict(path=bs.PATH_PARTITION, S=4096, layout=1, part_stream=1)),
-    ("blocks", dict(path=bs.PATH_PARTITION, S=4096, layout=2)),
 ]
 
 
@@ -131,12 +129,11 @@ def test_default_plan_n100k_range_2e20(ctx):
 def test_default_layout_by_scratch():
     # the capacity layout's buffer (about 4 bytes per value of the range) is
     # allowed up to 4 GiB, or up to twice the keys' own bytes: dense 2^31
-    # keys over 2^32 values use it (in blocks: many keys per bucket and
-    # partition CTA), sparse 2^24 keys over 2^32 values take the exact layout
-    # (no buffer beyond the output)
+    # keys over 2^32 values use it, sparse 2^24 keys over 2^32 values take
+    # the exact layout (no buffer beyond the output)
     c = bs.Context(0)
     try:
-        assert c.get_config(1 << 31, (1 << 32) - 1)["layout"] == "blocks"
+        assert c.get_config(1 << 31, (1 << 32) - 1)["layout"] == "capacity"
         assert c.get_config(1 << 24, (1 << 32) - 1)["layout"] == "exact"
         assert c.get_config(1 << 24, (1 << 28) - 1)["layout"] == "capacity"
     finally:
@@ -186,7 +183,7 @@ def test_duplicates_give_distinct_prefix(ctx, name, strat):
     check(ctx, keys, 3, **strat)
 
 
-@pytest.mark.parametrize("layout,persistent", [(1, 0), (1, 1), (2, 0)])
+@pytest.mark.parametrize("layout,persistent", [(1, 0), (1, 1)])
 def test_capacity_overflow_from_repeated_keys(ctx, layout, persistent):
     # one bucket receives more keys than it can hold (only possible with
     # repeats): that bucket is rebuilt from the whole input
@@ -199,12 +196,11 @@ def test_capacity_overflow_from_repeated_keys(ctx, layout, persistent):
 
 
 @pytest.mark.parametrize("order", ["random", "ascending", "descending", "runs"])
-@pytest.mark.parametrize("S", [1 << 15, 1 << 16, 50_048])
-def test_blocks_layout_refills_and_runs(ctx, order, S):
-    # 2^25 keys over 2^26 values in 1024 to 1341 buckets: each partition CTA
-    # (one per SM) takes several blocks of every bucket, so the blocks ahead
-    # are refilled many times; ordered inputs bring whole tiles of one bucket,
-    # which reserve runs of whole blocks at once
+@pytest.mark.parametrize("S,layout", [(1 << 15, 1), (1 << 16, 0), (50_048, 1)])
+def test_partition_of_ordered_inputs(ctx, order, S, layout):
+    # 2^25 keys over 2^26 values in 1024 to 1341 buckets (the partition at
+    # 1024 threads): ordered inputs bring whole tiles of one bucket, random
+    # order a few keys of every bucket per tile
     n, M = 1 << 25, 1 << 26
     keys = gen.feistel(gen.SEED_BASE + 61, n, M)
     if order == "ascending":
@@ -216,10 +212,10 @@ def test_blocks_layout_refills_and_runs(ctx, order, S):
         cuts = np.arange(0, n, 5000)
         perm = gen.shuffle(62, np.arange(cuts.size, dtype=np.uint32))
         keys = np.concatenate([srt[cuts[i]: cuts[i] + 5000] for i in perm])
-    check(ctx, keys, M - 1, path=bs.PATH_PARTITION, S=S, threads=512, layout=2)
+    check(ctx, keys, M - 1, path=bs.PATH_PARTITION, S=S, threads=512, layout=layout)
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2])
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("persistent", [0, 1])
 def test_repeats_spread_over_many_slices(ctx, layout, persistent):
     # repeated keys in many buckets: every slice after the first short one

@@ -145,9 +145,10 @@ def test_signed_default_context_entry(ctx):
     assert np.array_equal(out.cpu().numpy(), np.sort(keys))
 
 
-def test_blocks_layout_signed_bias(ctx):
-    # the blocks-layout partition classifies x - min_value: signed keys
-    # straddling zero, over 2048 buckets, with refills of the blocks ahead
+@pytest.mark.parametrize("layout", [0, 1])
+def test_wide_partition_signed_bias(ctx, layout):
+    # the partition classifies x - min_value: signed keys straddling zero,
+    # 2048 buckets (the partition at 1024 threads, buckets by shift)
     lo, hi = -(1 << 24), (1 << 24) - 1
     keys = signed_keys(64, 1 << 23, lo, hi)
-    check(ctx, keys, lo, hi, path=bs.PATH_PARTITION, S=1 << 14, threads=512, layout=2)
+    check(ctx, keys, lo, hi, path=bs.PATH_PARTITION, S=1 << 14, threads=512, layout=layout)

@@ -55,27 +55,13 @@ def test_sparse_full_range_exact_layout_wide_phases():
     assert sh["bucket_threads"] == 1024
 
 
-def test_dense_full_range_blocks_layout():
-    # 2^31 keys over 2^32 values (density 1/2): 4096 buckets of 2^20 values,
-    # about 2^19 keys per bucket and 3450 per bucket per partition CTA, so the
-    # partition takes each bucket's entries in blocks of 64 (one wave of one
-    # 1024-thread CTA per SM); the capacity per bucket is 2^20 plus two blocks
-    # per CTA; positions are staged
+def test_dense_full_range_capacity_layout():
+    # 2^31 keys over 2^32 values (density 1/2): the 16 GiB capacity buffer is
+    # twice the keys' bytes, which the rule allows; positions are staged
     cfg, sh = plan(1 << 31, 1 << 32)
-    assert cfg["path"] == "partition" and cfg["layout"] == "blocks"
-    assert sh["slices"] == 4096 and cfg["slice_values"] == 1 << 20
-    cap = (1 << 20) + 2 * SMS * 64
-    assert sh["scratch_bytes"] == 4096 * cap * 4 <= 9 * (1 << 31)
+    assert cfg["path"] == "partition" and cfg["layout"] == "capacity"
+    assert sh["scratch_bytes"] == 16 * GIB
     assert cfg["stage"] == 1 and sh["part_threads"] == 1024 and sh["bucket_threads"] == 512
-
-
-def test_blocks_layout_only_where_the_unused_blocks_are_few():
-    # the blocks left unused at the end (about 1.5 per bucket and CTA) must stay
-    # below 1/24 of the keys: 2^30 keys over 2^32 values have too few keys per
-    # bucket and CTA, and so have the benchmark's 2^24-key arrays
-    for n, M in [(1 << 30, 1 << 32), (1 << 24, 1 << 28), (1 << 24, 1 << 32)]:
-        cfg, _ = plan(n, M)
-        assert cfg["layout"] != "blocks", (n, M)
 
 
 NS = [1, 2, 31, 32, 33, 1000, 4097, 65_536, 65_537, 100_000, 1 << 20, (1 << 20) + 1, 1 << 22, 1 << 24, 1 << 26,
@@ -109,13 +95,6 @@ def test_plan_invariants(sms):
                 cap_bytes = sh["slices"] * min(S, n) * 4
                 if cfg["layout"] == "capacity":
                     assert sh["scratch_bytes"] == cap_bytes <= max(4 * GIB, 8 * n), where
-                elif cfg["layout"] == "blocks":
-                    # one wave of 1024-thread CTAs (one per SM); two blocks of 64 per CTA and bucket
-                    grid = min(sms, -(-n // sh["tile_keys"]))
-                    cap = -(-(min(S, n) + 2 * grid * 64) // 64) * 64
-                    assert sh["part_threads"] == 1024 and sh["slices"] >= 1024, where
-                    assert sh["scratch_bytes"] == sh["slices"] * cap * 4 <= max(4 * GIB, 9 * n), where
-                    assert 3 * sh["slices"] * 64 * sms * 24 <= 2 * n, where
                 else:
                     assert sh["scratch_bytes"] == 0 and cap_bytes > max(4 * GIB, 8 * n), where
                 assert cfg["stage"] <= int(10 * n >= M), where   # no staging below one key per ten values
