@@ -169,7 +169,7 @@ __device__ uint32_t block_exclusive_scan_u32(uint32_t nb, const uint32_t *c, uin
 
 // Calls f(key) for every key of p[lo, hi): 128-bit streaming loads for the
 // 16-byte aligned body, scalar loads for the peeled head and tail.
-template <int T, bool kStream, class F>
+template <int T, bool kStream, int U = 8, class F>
 __device__ __forceinline__ void for_each_key(const uint32_t *p, uint64_t lo, uint64_t hi, F &&f) {
     if (lo >= hi) return;
     const uint32_t mis = (uint32_t)((reinterpret_cast<uintptr_t>(p + lo) & 15u) >> 2);
@@ -180,12 +180,12 @@ __device__ __forceinline__ void for_each_key(const uint32_t *p, uint64_t lo, uin
     const uint64_t nv = (hi - b0) >> 2;
     const uint4 *v = reinterpret_cast<const uint4 *>(p + b0);
     uint64_t i = threadIdx.x;
-    for (; i + 7 * (uint64_t)T < nv; i += 8 * (uint64_t)T) {
-        uint4 q[8];
+    for (; i + (U - 1) * (uint64_t)T < nv; i += U * (uint64_t)T) {
+        uint4 q[U];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) q[u] = kStream ? __ldcs(v + i + u * T) : __ldcg(v + i + u * T);
+        for (int u = 0; u < U; ++u) q[u] = kStream ? __ldcs(v + i + u * T) : __ldcg(v + i + u * T);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < U; ++u) {
             f(q[u].x);
             f(q[u].y);
             f(q[u].z);
@@ -1056,14 +1056,24 @@ __device__ void part_tile_phase(const ArrayDesc &a, const uint32_t (&x)[kKeysPer
         if (kFull || br[j] != 0xFFFFFFFFu) sorted[hist[br[j] >> 16] + (br[j] & 0xFFFFu)] = x[j];
     }
     __syncthreads();
+    // (eight keys at a time: their loads, then their run words, then their
+    // stores, so that no key's shared-memory latency waits on another's)
     uint32_t *part = a.part;
-#pragma unroll 4
-    for (int j = 0; j < K; ++j) {
-        const uint32_t i = (uint32_t)j * T + threadIdx.x;
-        if (kFull || i < nkeys) {
-            const uint32_t v = sorted[i];
-            const uint2 f = run[part_bin<kShift, kCheck>(v, bias, maxv, sh, magic, nb)];
-            if (i < f.y) part[f.x + i] = v;
+#pragma unroll
+    for (int j0 = 0; j0 < K; j0 += 8) {
+        uint32_t v[8];
+        uint2 f[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t i = (uint32_t)(j0 + u) * T + threadIdx.x;
+            v[u] = (kFull || i < nkeys) ? sorted[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) f[u] = run[part_bin<kShift, kCheck>(v[u], bias, maxv, sh, magic, nb)];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t i = (uint32_t)(j0 + u) * T + threadIdx.x;
+            if ((kFull || i < nkeys) && i < f[u].y) part[f[u].x + i] = v[u];
         }
     }
     for (uint32_t i = lo_bin; i < hi_bin; ++i) hist[i] = 0u;
@@ -1325,7 +1335,7 @@ __device__ void slice_finish_sparse(const EngineParams &P, const ArrayDesc &a, u
     slice_complete<T>(a, m);
 }
 
-template <int T>
+template <int T, int U = 8>
 __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t b, char *smem, SharedMisc &m) {
     constexpr int NW = T / 32;
     const bool rank = a.emit == EMIT_RANK;
@@ -1409,26 +1419,26 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
         };
         if (filter_range) {
             const uint64_t M = a.M;
-            for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
+            for_each_key<T, false, U>(src, lo, hi, [&](uint32_t x) {
                 const uint32_t y = x - bias;
                 if ((uint64_t)y < M) set_bits(y);
                 else bad = true;
             });
         } else {
-            for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
+            for_each_key<T, false, U>(src, lo, hi, [&](uint32_t x) {
                 const uint32_t l = x - base;
                 if (l < span) set_bits(l);
             });
         }
     } else if (filter_range) {
         const uint64_t M = a.M;
-        for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
+        for_each_key<T, false, U>(src, lo, hi, [&](uint32_t x) {
             const uint32_t y = x - bias;
             if ((uint64_t)y < M) atomicOr(&bm[y >> 5], 1u << (y & 31));
             else bad = true;
         });
     } else {
-        for_each_key<T, false>(src, lo, hi, [&](uint32_t x) {
+        for_each_key<T, false, U>(src, lo, hi, [&](uint32_t x) {
             const uint32_t l = x - base;
             if (l < span) atomicOr(&bm[l >> 5], 1u << (l & 31));
         });
@@ -1630,9 +1640,15 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // each phase runs with the occupancy its shared memory allows.  Slice phases
 // take their slices in ticket order (the look-back needs it); tile phases use
 // a grid-stride loop.
-// at most 64 registers per thread: 1024 threads (four CTAs of 256) fit one SM
-template <int T, int TYPE>
-__global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constant__ EngineParams P) {
+// MINB = 1024 / T: at most 64 registers per thread, so that 1024 threads
+// (four CTAs of 256, two of 512) fit one SM.  MINB = 1 (a "solo" kernel) is
+// launched when the phase's shared memory leaves room for one CTA per SM
+// only: the CTA then gets the whole register file (up to 255 registers a
+// thread at 256 threads, 128 at 512), and the bucket scatter keeps 16
+// 16-byte loads in flight per thread instead of 8.
+template <int T, int TYPE, int MINB = 1024 / T>
+__global__ void __launch_bounds__(T, MINB) phase_kernel(const __grid_constant__ EngineParams P) {
+    constexpr int U = (MINB == 1 && T <= 512) ? 16 : 8;
     extern __shared__ __align__(16) char smem[];
     __shared__ SharedMisc m;
     if (threadIdx.x == 0) {
@@ -1650,7 +1666,7 @@ __global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constan
         if (threadIdx.x == 0) m.defer = 1u;
         __syncthreads();
         for (uint32_t t = blockIdx.x; t < P.total_items; t += gridDim.x) {
-            item_bucket<T>(P, a, t, smem, m);
+            item_bucket<T, U>(P, a, t, smem, m);
             __syncthreads();
         }
         pdl_trigger();
@@ -1664,7 +1680,7 @@ __global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constan
             const uint32_t t = m.ticket;
             __syncthreads();
             if (t >= P.total_items) break;
-            if constexpr (TYPE == IT_BUCKET) item_bucket<T>(P, a, t, smem, m);
+            if constexpr (TYPE == IT_BUCKET) item_bucket<T, U>(P, a, t, smem, m);
             else item_gscan<T>(P, a, t, smem, m);
             __syncthreads();
         }
@@ -1700,9 +1716,22 @@ __global__ void __launch_bounds__(T, 1024 / T) phase_kernel(const __grid_constan
 // ------------------------------------------------------------------- host
 using KernelFn = void (*)(EngineParams);
 
-// kind: -1 = persistent engine, else an ItemType (one phase)
-static KernelFn kernel_for(int kind, int threads) {
+// A phase whose dynamic shared memory is above this leaves room for one CTA
+// per SM (of the 228 KiB of an SM), so its solo kernel (MINB = 1) is used.
+constexpr uint32_t kSoloSmemBytes = 114u * 1024u - 1024u;
+
+// kind: -1 = persistent engine, else an ItemType (one phase); solo: the
+// MINB = 1 instance of a phase kernel (256 / 512 threads)
+static KernelFn kernel_for(int kind, int threads, bool solo = false) {
     if (threads == 256) {
+        if (solo) {
+            switch (kind) {
+                case IT_PART: return phase_kernel<256, IT_PART, 1>;
+                case IT_BUCKET: return phase_kernel<256, IT_BUCKET, 1>;
+                case IT_GSCAN: return phase_kernel<256, IT_GSCAN, 1>;
+                case IT_PARTS: return phase_kernel<256, IT_PARTS, 1>;
+            }
+        }
         switch (kind) {
             case -1: return engine_kernel<256>;
             case IT_HIST: return phase_kernel<256, IT_HIST>;
@@ -1713,6 +1742,14 @@ static KernelFn kernel_for(int kind, int threads) {
             case IT_PARTS: return phase_kernel<256, IT_PARTS>;
         }
     } else if (threads == 512) {
+        if (solo) {
+            switch (kind) {
+                case IT_PART: return phase_kernel<512, IT_PART, 1>;
+                case IT_BUCKET: return phase_kernel<512, IT_BUCKET, 1>;
+                case IT_GSCAN: return phase_kernel<512, IT_GSCAN, 1>;
+                case IT_PARTS: return phase_kernel<512, IT_PARTS, 1>;
+            }
+        }
         switch (kind) {
             case -1: return engine_kernel<512>;
             case IT_HIST: return phase_kernel<512, IT_HIST>;
@@ -1737,6 +1774,13 @@ static KernelFn kernel_for(int kind, int threads) {
     return nullptr;
 }
 
+// the kernel a phase launches with `smem_bytes` of dynamic shared memory
+static KernelFn kernel_for_smem(int kind, int threads, uint32_t smem_bytes) {
+    const bool solo = kind >= 0 && threads < 1024 && smem_bytes > kSoloSmemBytes;
+    KernelFn f = solo ? kernel_for(kind, threads, true) : nullptr;
+    return f ? f : kernel_for(kind, threads);
+}
+
 int engine_set_smem_limit(int threads, uint32_t smem_bytes) {
     for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN, (int)IT_PARTS}) {
         if (kind == -1 && threads == 1024) continue;   // no persistent engine at 1024 threads
@@ -1744,6 +1788,11 @@ int engine_set_smem_limit(int threads, uint32_t smem_bytes) {
         if (!f) return (int)cudaErrorInvalidValue;
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
         if (e != cudaSuccess) return (int)e;
+        KernelFn g = threads < 1024 ? kernel_for(kind, threads, true) : nullptr;
+        if (g && g != f) {
+            e = cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+            if (e != cudaSuccess) return (int)e;
+        }
     }
     return 0;
 }
@@ -1753,7 +1802,7 @@ int engine_max_blocks_per_sm(int threads, uint32_t smem_bytes, int *blocks) {
 }
 
 int kernel_max_blocks_per_sm(int kind, int threads, uint32_t smem_bytes, int *blocks) {
-    KernelFn f = kernel_for(kind, threads);
+    KernelFn f = kernel_for_smem(kind, threads, smem_bytes);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem_bytes);
 }
@@ -1764,7 +1813,7 @@ int engine_launch(const EngineParams &p, int threads, uint32_t smem_bytes, int g
 
 int kernel_launch(int kind, const EngineParams &p, int threads, uint32_t smem_bytes, int grid, void *stream,
                   bool pdl) {
-    KernelFn f = kernel_for(kind, threads);
+    KernelFn f = kernel_for_smem(kind, threads, smem_bytes);
     if (!f) return (int)cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
