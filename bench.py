@@ -248,7 +248,7 @@ def run_plain(args, w, ws, rank, local):
     if args.path:
         ctx.set_config(n, M - 1, {"fused": 1, "partition": 2, "global": 3}[args.path], args.slice, args.threads,
                        words_per_lane=args.wpl, stage=args.stage, layout=args.layout, persistent=args.persistent,
-                       emit=args.emit, part_stream=args.part_stream)
+                       emit=args.emit, part_stream=args.part_stream, part_threads=args.part_threads)
     cfg = ctx.get_config(n, M - 1)
     flush = L2Flush(args.flush)
     stream = torch.cuda.current_stream()
@@ -685,6 +685,7 @@ def main():
     ap.add_argument("--persistent", type=int, default=0)
     ap.add_argument("--emit", type=int, default=0)
     ap.add_argument("--part-stream", type=int, default=0)
+    ap.add_argument("--part-threads", type=int, default=0)
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cub", action="store_true")

@@ -136,6 +136,19 @@ bitsort_status_t bitsort_ex(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n
 bitsort_status_t bitsort_i32(bitsort_ctx_t *ctx, const int32_t *keys, uint64_t n, int32_t min_value,
                              int32_t max_value, int32_t *out, bitsort_result_t *d_result, bitsort_stream_t stream);
 
+/* Sort unsigned keys bounded below and above: distinct uint32 keys in
+ * [min_value, max_value] (the bitmap covers max_value - min_value + 1
+ * values; the same shift as bitsort_i32, without the signed reading).  One
+ * rank's share of a sort spread over GPUs by value range (see
+ * bitsort_range_split) is such an array.  Same contract as bitsort_i32:
+ * keys == out sorts in place; min_value > max_value, n above the span,
+ * overlaps or misalignment -> BITSORT_ERR_INVALID; keys outside the range ->
+ * BITSORT_ERR_KEY_RANGE, repeats -> BITSORT_ERR_DUPLICATE through d_result
+ * (or the context). */
+bitsort_status_t bitsort_span(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n, uint32_t min_value,
+                              uint32_t max_value, uint32_t *out, bitsort_result_t *d_result,
+                              bitsort_stream_t stream);
+
 /* The bitmap sort for keys stored in 16, 8 and 64 bits (Algorithm 1 is
  * written for any integer type T; Section V).  Same contract as bitsort_ex()
  * (distinct keys bounded by max_value, keys == out allowed, other overlaps,
@@ -234,6 +247,38 @@ bitsort_status_t bitsort_sync_status(bitsort_ctx_t *ctx, bitsort_stream_t stream
  * Allocates nothing: no cudaMalloc/cudaFree, no library allocation. */
 bitsort_status_t bitsort_noalloc(const uint32_t *keys, uint64_t n, uint32_t max_value, uint32_t *out,
                                  bitsort_result_t *d_result, bitsort_stream_t stream);
+
+/* --------------------------------------------------------------- multi-GPU */
+
+/* One sort of Section V's problem (one array, one ascending result) spread
+ * over G GPUs by value range: rank g owns the values [g*W, (g+1)*W) with
+ * W = bitsort_range_width(max_value, G).  Each rank groups its keys by owner
+ * (bitsort_range_split), the ranks exchange the groups (an all-to-all of the
+ * G counts, then of the keys; the host's collective library, not this
+ * library, moves them), and each rank sorts what it received with
+ * bitsort_span(ctx, keys, n, g*W, min((g+1)*W, M) - 1, ...).  Rank g's output
+ * is then the g-th piece of the sorted array; its offset is the sum of the
+ * counts of the ranks before it (an all-gather of G counts).  The exchange
+ * and the offsets are host logic (paper_1312_0138_gb300/shard.py).
+ *
+ * bitsort_range_width: W for G = parts ranks: ceil((max_value + 1) / parts)
+ * rounded up to a multiple of 128 (0 for parts == 0).
+ *
+ * bitsort_range_split: keys (DEVICE, n uint32) grouped by owner into out
+ * (DEVICE, n entries, not overlapping keys): group g at [o_g, o_g + c_g),
+ * the groups in rank order, the keys of a group in no particular order.
+ *   - d_counts: DEVICE pointer to `parts` uint64 receiving c_0 .. c_{parts-1}.
+ *   - parts in 1 .. 8192; keys == out, overlaps, misalignment, n >= 2^32 or
+ *     a null d_counts -> BITSORT_ERR_INVALID.
+ *   - Keys above max_value are left out of every group and reported as
+ *     BITSORT_ERR_KEY_RANGE through d_result (or the context), whose count is
+ *     the number of keys grouped.  Distinctness is not checked here (each
+ *     rank's bitsort_span does that).
+ *   - Uses the context's scratch and leaves it at zero; enqueued on `stream`. */
+uint64_t bitsort_range_width(uint32_t max_value, uint32_t parts);
+bitsort_status_t bitsort_range_split(bitsort_ctx_t *ctx, const uint32_t *keys, uint64_t n, uint32_t max_value,
+                                     uint32_t parts, uint32_t *out, uint64_t *d_counts, bitsort_result_t *d_result,
+                                     bitsort_stream_t stream);
 
 /* ---------------------------------------------------------------- batching */
 
@@ -350,6 +395,9 @@ typedef enum {
  *                   also sets a summary bitmap (one bit per non-empty word)
  *                   and counts and emits only the non-empty words, clearing
  *                   them behind; 0: every slice walks all its words.
+ *   part_threads    block size of the histogram and partition phases of a
+ *                   one-kernel-per-phase plan (256, 512 or 1024); 0 = the
+ *                   built-in rule (512 threads, 1024 from 1024 buckets).
  *   ms              measured time when tuned (output only). */
 typedef struct {
     int32_t path;
@@ -362,6 +410,8 @@ typedef struct {
     uint32_t emit;
     uint32_t part_stream;
     uint32_t summary;
+    uint32_t part_threads;
+    uint32_t reserved;
     double ms;
 } bitsort_config_t;
 

@@ -40,6 +40,7 @@ EXPORTS = [
     "bitsort_tune_save", "bitsort_tune_load", "bitsort_set_wait_limit_ms", "bitsort_debug_stalled_launch",
     "bitsort_kernel_launches", "bitsort_noalloc", "bitsort_set_phase_timing", "bitsort_phase_times",
     "bitsort_set_batch_config", "bitsort_get_batch_config", "bitsort_batch_autotune", "bitsort_plan_rule",
+    "bitsort_span", "bitsort_range_width", "bitsort_range_split",
 ]
 
 
@@ -66,14 +67,15 @@ class Config(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("slice_values", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("words_per_lane", ctypes.c_uint32), ("stage", ctypes.c_uint32), ("layout", ctypes.c_uint32),
                 ("persistent", ctypes.c_uint32), ("emit", ctypes.c_uint32), ("part_stream", ctypes.c_uint32),
-                ("summary", ctypes.c_uint32), ("ms", ctypes.c_double)]
+                ("summary", ctypes.c_uint32), ("part_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"path": PATH_NAMES.get(self.path, self.path), "slice_values": self.slice_values,
                 "threads": self.block_threads, "words_per_lane": self.words_per_lane, "stage": self.stage,
                 "layout": LAYOUT_NAMES.get(self.layout, self.layout), "persistent": self.persistent,
                 "emit": EMIT_NAMES.get(self.emit, self.emit), "part_stream": self.part_stream,
-                "summary": self.summary, "ms": self.ms}
+                "summary": self.summary, "part_threads": self.part_threads, "ms": self.ms}
 
 
 LAYOUT_EXACT, LAYOUT_CAPACITY = 0, 1
@@ -107,6 +109,9 @@ def _declare(lib):
         "bitsort": (st, [p, ctypes.c_size_t, u32, p, p]),
         "bitsort_ex": (st, [p, p, u64, u32, p, p, p]),
         "bitsort_i32": (st, [p, p, u64, ctypes.c_int32, ctypes.c_int32, p, p, p]),
+        "bitsort_span": (st, [p, p, u64, u32, u32, p, p, p]),
+        "bitsort_range_width": (u64, [u32, u32]),
+        "bitsort_range_split": (st, [p, p, u64, u32, u32, p, p, p, p]),
         "bitsort_host": (st, [p, p, u64, u32, p, p, p]),
         "bitsort_multiset": (st, [p, p, u64, u32, u32, p, p, p]),
         "bitsort_u16": (st, [p, p, u64, ctypes.c_uint16, p, p, p]),
@@ -254,6 +259,35 @@ class Context:
         st, cnt = self.sync_status(stream)
         return st, cnt, out
 
+    def sort_span_async(self, keys, min_value: int, max_value: int, out=None, result=None, stream=None):
+        """Enqueue the sort of distinct uint32 `keys` in [min_value, max_value]
+        (C entry point bitsort_span); returns out."""
+        import torch
+        if out is None:
+            out = torch.empty_like(keys)
+        rptr = result.data_ptr() if result is not None else None
+        st = load().bitsort_span(self.handle, _ptr(keys) if keys.numel() else None, keys.numel(), int(min_value),
+                                 int(max_value), _ptr(out) if out.numel() else None, rptr, _stream_handle(stream))
+        _check(st, "bitsort_span")
+        return out
+
+    def range_split_async(self, keys, max_value: int, parts: int, out=None, counts=None, result=None,
+                          stream=None):
+        """Enqueue the grouping of `keys` by the rank that owns their value
+        range (C entry point bitsort_range_split); returns (out, counts), counts
+        a device int64 tensor of `parts` group sizes."""
+        import torch
+        if out is None:
+            out = torch.empty_like(keys)
+        if counts is None:
+            counts = torch.empty(parts, dtype=torch.int64, device=keys.device)
+        rptr = result.data_ptr() if result is not None else None
+        st = load().bitsort_range_split(self.handle, _ptr(keys) if keys.numel() else None, keys.numel(),
+                                        int(max_value), int(parts), _ptr(out) if out.numel() else None,
+                                        _ptr(counts, (torch.int64,)), rptr, _stream_handle(stream))
+        _check(st, "bitsort_range_split")
+        return out, counts
+
     def sort_width_async(self, keys, max_value: int, out=None, result=None, stream=None):
         """Bitmap sort of 16-, 8- or 64-bit keys (torch int16 / uint8 / int64
         tensors holding the unsigned values); returns out."""
@@ -337,9 +371,9 @@ class Context:
     # tuning ----------------------------------------------------------------
     def set_config(self, n: int, max_value: int, path: int, slice_values: int = 0, threads: int = 0,
                    words_per_lane: int = 0, stage: int = 0, layout: int = LAYOUT_CAPACITY, persistent: int = 0,
-                   emit: int = EMIT_WORD, part_stream: int = 0, summary: int = 1):
+                   emit: int = EMIT_WORD, part_stream: int = 0, summary: int = 1, part_threads: int = 0):
         cfg = Config(path, slice_values, threads, words_per_lane, stage, layout, persistent, emit, part_stream,
-                     summary, 0.0)
+                     summary, part_threads, 0, 0.0)
         _check(load().bitsort_set_config(self.handle, n, max_value, ctypes.byref(cfg)), "bitsort_set_config")
 
     def get_config(self, n: int, max_value: int):
@@ -399,7 +433,7 @@ class Context:
 
     def set_batch_config(self, path: int = PATH_PARTITION, slice_values: int = 0, threads: int = 0,
                          words_per_lane: int = 0, stage: int = 0):
-        cfg = Config(path, slice_values, threads, words_per_lane, stage, 0, 1, 0, 0, 1, 0.0)
+        cfg = Config(path, slice_values, threads, words_per_lane, stage, 0, 1, 0, 0, 1, 0, 0, 0.0)
         _check(load().bitsort_set_batch_config(self.handle, ctypes.byref(cfg)), "bitsort_set_batch_config")
 
     def get_batch_config(self):
@@ -540,6 +574,12 @@ def bitsort_noalloc(keys, max_value: int, out, result, stream=None):
                                 _ptr(out) if out.numel() else None, result.data_ptr(), _stream_handle(stream))
     _check(st, "bitsort_noalloc")
     return out
+
+
+def range_width(max_value: int, parts: int) -> int:
+    """Values per rank of a sort spread over `parts` ranks by value range
+    (C entry point bitsort_range_width)."""
+    return int(load().bitsort_range_width(int(max_value), int(parts)))
 
 
 def sync_status(stream=None):

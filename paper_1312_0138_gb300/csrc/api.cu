@@ -260,6 +260,8 @@ bsx_config bsx_lookup_config(bitsort_ctx *c, uint64_t n, uint64_t M) {
 bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
     if (cfg.threads != 256 && cfg.threads != 512 && cfg.threads != 1024) cfg.threads = 512;
     if (cfg.threads == 1024 && cfg.persistent) cfg.threads = 512;   // the persistent engine has 256 / 512
+    if (cfg.part_threads != 0 && cfg.part_threads != 256 && cfg.part_threads != 512 && cfg.part_threads != 1024)
+        cfg.part_threads = 0;
     if (cfg.wpl != 1 && cfg.wpl != 2 && cfg.wpl != 4 && cfg.wpl != 8) cfg.wpl = 2;
     if (cfg.stage && cfg.wpl == 2) cfg.wpl = 1;    // staged emission: 1, 4 or 8 words per lane
     if (!cfg.stage && cfg.wpl == 8) cfg.wpl = 4;   // direct emission: 1, 2 or 4
@@ -461,7 +463,11 @@ void bsx_plan_single(int sms, uint32_t smem_optin, const bsx_config &cfg0, uint6
     const bool partitioned = a.path == BITSORT_PATH_PARTITION;
     pl.stream_part = !cfg.persistent && partitioned && keys_aligned && cfg.stream_part;
     int Tp = T, Tb = T;
-    if (!cfg.persistent && T == 512 && partitioned) {
+    if (!cfg.persistent && partitioned && cfg.part_threads) {
+        const uint32_t tk = (uint32_t)(kKeysPerThread * cfg.part_threads);
+        const uint32_t ps = pl.stream_part ? part_stream_smem_bytes(a.nslices, tk) : part_phase_smem_bytes(a.nslices, tk);
+        if (ps <= smem_optin) Tp = cfg.part_threads;
+    } else if (!cfg.persistent && T == 512 && partitioned) {
         const uint32_t wide = (uint32_t)(kKeysPerThread * 1024);
         const uint32_t part_smem =
             pl.stream_part ? part_stream_smem_bytes(a.nslices, wide) : part_phase_smem_bytes(a.nslices, wide);
@@ -671,6 +677,26 @@ extern "C" bitsort_status_t bitsort_i32(bitsort_ctx_t *c, const int32_t *keys, u
     return launch_single(c, cfg, k, n, M, o, d_result, s, 0, bias);
 }
 
+extern "C" bitsort_status_t bitsort_span(bitsort_ctx_t *c, const uint32_t *keys, uint64_t n, uint32_t min_value,
+                                         uint32_t max_value, uint32_t *out, bitsort_result_t *d_result,
+                                         bitsort_stream_t stream) {
+    bsx_range nvtx_range_("bitsort_span");
+    if (!c) c = bsx_default_ctx();
+    if (!c) return BITSORT_ERR_CUDA;
+    if (min_value > max_value) return BITSORT_ERR_INVALID;
+    // keys in [min_value, max_value] are classified as x - min_value, the
+    // offsets 0 .. max_value - min_value, and written back unshifted
+    const uint32_t span_max = max_value - min_value;
+    bitsort_status_t st = bsx_validate(keys, n, span_max, out);
+    if (st != BITSORT_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(c->device) != cudaSuccess) return BITSORT_ERR_CUDA;
+    if (n == 0) return write_trivial_result(c, d_result, s);
+    const uint64_t M = (uint64_t)span_max + 1;
+    bsx_config cfg = bsx_lookup_config(c, n, M);
+    return launch_single(c, cfg, keys, n, M, out, d_result, s, 0, min_value);
+}
+
 extern "C" bitsort_status_t bitsort_host(bitsort_ctx_t *c, const uint32_t *h_keys, uint64_t n, uint32_t max_value,
                                          uint32_t *h_out, bitsort_result_t *h_result, bitsort_stream_t stream) {
     bsx_range nvtx_range_("bitsort_host");
@@ -801,6 +827,8 @@ static void to_public(const bsx_config &c, bitsort_config_t *o) {
     o->emit = c.emit;
     o->part_stream = c.stream_part ? 1 : 0;
     o->summary = c.summary ? 1 : 0;
+    o->part_threads = (uint32_t)c.part_threads;
+    o->reserved = 0;
     o->ms = c.ms;
 }
 
@@ -827,6 +855,7 @@ extern "C" bitsort_status_t bitsort_set_config(bitsort_ctx_t *c, uint64_t n, uin
     cfg.emit = in->emit;
     cfg.stream_part = in->part_stream != 0;
     cfg.summary = in->summary != 0;
+    cfg.part_threads = (int)in->part_threads;
     c->table[key] = bsx_sanitize(cfg, n, M);
     return BITSORT_OK;
 }
@@ -925,6 +954,18 @@ std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_
         push(BITSORT_PATH_PARTITION, ceil_div(M, 2ull * c->sms), threads, 1, true, LAYOUT_CAPACITY);
         push(BITSORT_PATH_PARTITION, ceil_div(M, 2ull * c->sms), threads, 1, true, LAYOUT_EXACT);
     }
+    // the partition phase at each block size (the rule takes 1024 threads
+    // from 1024 buckets, else the plan's)
+    const size_t base_count = out.size();
+    for (size_t k = 0; k < base_count; ++k) {
+        const bsx_config b = out[k];
+        if (b.path != BITSORT_PATH_PARTITION || b.persistent || b.part_threads) continue;
+        for (int pt : {512, 1024}) {
+            bsx_config v = b;
+            v.part_threads = pt;
+            out.push_back(v);
+        }
+    }
     // shared memory must fit
     std::vector<bsx_config> fit;
     for (auto &cfg : out) {
@@ -1013,16 +1054,17 @@ extern "C" bitsort_status_t bitsort_tune_save(bitsort_ctx_t *c, const char *path
     FILE *f = fopen(path, "w");
     if (!f) return BITSORT_ERR_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
-    fprintf(f, "{\"version\": 1, \"entries\": [");
+    fprintf(f, "{\"version\": 2, \"entries\": [");
     bool first = true;
     for (auto &kv : c->table) {
         const bsx_config &g = kv.second;
         fprintf(f,
                 "%s\n  {\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
                 "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"part_stream\": %d, "
-                "\"summary\": %d, \"ms\": %.6f}",
+                "\"summary\": %d, \"part_threads\": %d, \"ms\": %.6f}",
                 first ? "" : ",", kv.first.first, kv.first.second, (int)g.path, g.S, g.threads, g.wpl,
-                g.stage ? 1 : 0, g.layout, g.persistent ? 1 : 0, g.emit, g.stream_part ? 1 : 0, g.summary ? 1 : 0, g.ms);
+                g.stage ? 1 : 0, g.layout, g.persistent ? 1 : 0, g.emit, g.stream_part ? 1 : 0, g.summary ? 1 : 0,
+                g.part_threads, g.ms);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -1043,15 +1085,25 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
     std::map<std::pair<int, int>, bsx_config> table;
     size_t pos = 0;
     while ((pos = text.find("{\"log2n\"", pos)) != std::string::npos) {
-        int ln = 0, lm = 0, p = 0, th = 0, stage = 0, pers = 0, pstream = 0, summary = 1;
+        int ln = 0, lm = 0, p = 0, th = 0, stage = 0, pers = 0, pstream = 0, summary = 1, pth = 0;
         unsigned S = 0, wpl = 0, layout = 0, emit = 0;
         double ms = 0;
-        if (sscanf(text.c_str() + pos,
+        // version 2 entries carry part_threads; version 1 entries do not
+        const char *entry = text.c_str() + pos;
+        const int got2 = sscanf(entry,
                    "{\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
                    "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"part_stream\": %d, "
-                   "\"summary\": %d, \"ms\": %lf",
-                   &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &emit, &pstream, &summary, &ms) != 13)
-            return BITSORT_ERR_INVALID;
+                   "\"summary\": %d, \"part_threads\": %d, \"ms\": %lf",
+                   &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &emit, &pstream, &summary, &pth, &ms);
+        if (got2 != 14) {
+            pth = 0;
+            if (sscanf(entry,
+                       "{\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
+                       "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, "
+                       "\"part_stream\": %d, \"summary\": %d, \"ms\": %lf",
+                       &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &emit, &pstream, &summary, &ms) != 13)
+                return BITSORT_ERR_INVALID;
+        }
         if (p < 1 || p > 3 || (th != 256 && th != 512 && th != 1024) || ln < 0 || ln > 64 || lm < 0 || lm > 33)
             return BITSORT_ERR_INVALID;
         bsx_config cfg;
@@ -1065,6 +1117,7 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
         cfg.emit = emit;
         cfg.stream_part = pstream != 0;
         cfg.summary = summary != 0;
+        cfg.part_threads = pth;
         cfg.ms = ms;
         table[std::make_pair(ln, lm)] = cfg;
         ++pos;

@@ -25,6 +25,7 @@ struct bsx_config {
     uint32_t emit = 0;       // bsx::EMIT_WORD (0) or bsx::EMIT_RANK (1)
     bool summary = true;     // sparse slices keep a summary bitmap (word emission)
     bool stream_part = false; // phased PARTITION: stream tiles through bulk copies when keys are 16-byte aligned
+    int part_threads = 0;     // phased PARTITION: block size of the HIST/PART phases (0 = the plan's rule)
     double ms = 0;           // measured time when tuned (0 = not measured)
 };
 

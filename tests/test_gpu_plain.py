@@ -75,6 +75,10 @@ CONFIGS = [
     ("exact_S1M_w2_pow2", bs.PATH_PARTITION, 1 << 20, 512, dict(layout=0, words_per_lane=2)),
     ("cap_odd_256", bs.PATH_PARTITION, 300_032, 256, dict(layout=1)),
     ("cap_odd_1024", bs.PATH_PARTITION, 883_072, 1024, dict(layout=1)),
+    # the partition phase at a block size of its own
+    ("cap_S4096_part512", bs.PATH_PARTITION, 4096, 512, dict(layout=1, part_threads=512)),
+    ("exact_S4096_part256", bs.PATH_PARTITION, 4096, 512, dict(layout=0, part_threads=256)),
+    ("cap_S64K_part1024_stage", bs.PATH_PARTITION, 1 << 16, 512, dict(layout=1, part_threads=1024, stage=1)),
 ]
 
 
