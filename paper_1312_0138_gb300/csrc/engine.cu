@@ -962,15 +962,42 @@ __device__ __forceinline__ uint2 part_run(const ArrayDesc &a, uint32_t i, uint32
     return make_uint2(base + at - p, fit + p);
 }
 
+// Keys of tile t into x (element j*T + threadIdx.x in x[j]): 16-byte loads
+// for a whole tile of 16-byte aligned keys; returns the tile's key count.
+template <int T>
+__device__ __forceinline__ uint32_t part_load(const ArrayDesc &a, uint32_t t, uint32_t (&x)[kKeysPerThread]) {
+    constexpr int K = kKeysPerThread;
+    const uint64_t lo = (uint64_t)t * a.tile_keys;
+    const uint32_t nkeys = (uint32_t)(min(lo + a.tile_keys, a.n) - lo);
+    if (nkeys == a.tile_keys && (reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.keys + lo);
+#pragma unroll
+        for (int j = 0; j < K / 4; ++j) {
+            const uint4 q = __ldcs(src + j * T + threadIdx.x);
+            x[4 * j] = q.x; x[4 * j + 1] = q.y; x[4 * j + 2] = q.z; x[4 * j + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const uint32_t e = (uint32_t)j * T + threadIdx.x;
+            x[j] = e < nkeys ? __ldcs(a.keys + lo + e) : 0u;
+        }
+    }
+    return nkeys;
+}
+
 // One tile: x[j] holds tile element j*T + threadIdx.x (valid while below
 // nkeys; every element when kFull).  The thread owns buckets [lo_bin,
 // hi_bin) (the discard bin nb, keys above max_value, comes after all of
 // them and is never written); it zeroes their counts again at the end, so
-// that the next tile starts with an empty histogram.  Ends with a barrier.
+// that the next tile starts with an empty histogram.  Once the reorder has
+// used x, the keys of tile `next` (if below key_tiles) are loaded into it,
+// so that their round trip overlaps this tile's write-out.  Ends with a
+// barrier.
 template <int T, bool kShift, bool kCheck, bool kFull>
-__device__ void part_tile_phase(const ArrayDesc &a, const uint32_t (&x)[kKeysPerThread], uint32_t nkeys,
-                                uint32_t *hist, const uint32_t *base, uint2 *run, uint32_t *sorted, uint32_t lo_bin,
-                                uint32_t hi_bin, SharedMisc &m) {
+__device__ void part_tile_phase(const ArrayDesc &a, uint32_t (&x)[kKeysPerThread], uint32_t nkeys, uint32_t *hist,
+                                const uint32_t *base, uint2 *run, uint32_t *sorted, uint32_t lo_bin, uint32_t hi_bin,
+                                SharedMisc &m, uint32_t next) {
     constexpr int K = kKeysPerThread;
     constexpr int NW = T / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1058,6 +1085,7 @@ __device__ void part_tile_phase(const ArrayDesc &a, const uint32_t (&x)[kKeysPer
     __syncthreads();
     // (eight keys at a time: their loads, then their run words, then their
     // stores, so that no key's shared-memory latency waits on another's)
+    if (next < a.key_tiles) part_load<T>(a, next, x);
     uint32_t *part = a.part;
 #pragma unroll
     for (int j0 = 0; j0 < K; j0 += 8) {
@@ -1101,30 +1129,21 @@ __device__ void part_phase(const EngineParams &P, const ArrayDesc &a, char *smem
     __syncthreads();
     const bool shift = a.s_shift != 0;
     const bool check = a.M != (1ull << 32);
-    for (uint32_t t = blockIdx.x; t < a.key_tiles; t += gridDim.x) {
-        const uint64_t lo = (uint64_t)t * a.tile_keys;
-        const uint32_t nkeys = (uint32_t)(min(lo + a.tile_keys, a.n) - lo);
-        const bool full = nkeys == a.tile_keys && (reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0;
-        uint32_t x[K];
-        if (full) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(a.keys + lo);
-#pragma unroll
-            for (int j = 0; j < K / 4; ++j) {
-                const uint4 q = __ldcs(src + j * T + threadIdx.x);
-                x[4 * j] = q.x; x[4 * j + 1] = q.y; x[4 * j + 2] = q.z; x[4 * j + 3] = q.w;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const uint32_t e = (uint32_t)j * T + threadIdx.x;
-                x[j] = e < nkeys ? __ldcs(a.keys + lo + e) : 0u;
-            }
-        }
-        if (!full) part_tile_phase<T, false, true, false>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
-        else if (shift && check) part_tile_phase<T, true, true, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
-        else if (shift) part_tile_phase<T, true, false, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
-        else if (check) part_tile_phase<T, false, true, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
-        else part_tile_phase<T, false, false, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m);
+    const bool aligned = (reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0;
+    uint32_t t = blockIdx.x;
+    if (t >= a.key_tiles) return;
+    uint32_t x[K];
+    uint32_t nkeys = part_load<T>(a, t, x);
+    while (t < a.key_tiles) {
+        const uint32_t next = t + gridDim.x;
+        const bool full = nkeys == a.tile_keys && aligned;
+        if (!full) part_tile_phase<T, false, true, false>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next);
+        else if (shift && check) part_tile_phase<T, true, true, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next);
+        else if (shift) part_tile_phase<T, true, false, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next);
+        else if (check) part_tile_phase<T, false, true, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next);
+        else part_tile_phase<T, false, false, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next);
+        t = next;
+        if (t < a.key_tiles) nkeys = (uint32_t)(min((uint64_t)(t + 1) * a.tile_keys, a.n) - (uint64_t)t * a.tile_keys);
     }
 }
 

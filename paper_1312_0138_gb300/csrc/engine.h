@@ -158,7 +158,8 @@ inline uint32_t hist_smem_bytes(uint32_t nslices) { return nslices * 4u; }
 // PART phase kernel: per bin (plus the discard bin) count / prefix, bucket
 // base and run words; the tile
 inline uint32_t part_phase_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
-    return (((nslices + 1) * 8u + 7u) & ~7u) + (nslices + 1) * 8u + tile_keys * 4u + 16u;
+    const uint32_t nq = (nslices + 1 + 3) & ~3u;   // each per-bin array rounded to 16 bytes
+    return nq * 16u + tile_keys * 4u + 16u;
 }
 // streaming PART: bins, bucket tags, two landing buffers, two mbarriers (128-byte aligned parts)
 inline uint32_t part_stream_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
