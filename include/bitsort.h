@@ -329,17 +329,24 @@ typedef struct bitsort_server bitsort_server_t;
 
 /* A continuous-batching sort server on `device`.  Requests are admitted in
  * arrival order while the bytes their bitmap and output need
- * (ceil(M/8) + 4n, M = max_value + 1) fit in `budget_bytes`; admitted
- * requests are launched at once: a request of at least 2^22 keys alone as a
- * plain sort, smaller ones together as batches of up to 64 MiB of work
- * (8n + M/4 bytes each).  `max_inflight` streams (1..64) take the batches,
- * each holding up to four queued behind one another, so that the device
- * never waits for the scheduler and work on different streams overlaps. */
+ * (ceil(M/8) + 4n, M = max_value + 1), plus the device memory the server's
+ * stream contexts keep (their partition buffers and global bitmaps, held at
+ * their high-water sizes) and the growth of that memory a request's plain
+ * sort asks for, fit in `budget_bytes`.  Admitted requests are launched at
+ * once: a request of at least 2^22 keys alone as a plain sort, smaller ones
+ * together as batches of up to 64 MiB of work (8n + M/4 bytes each).
+ * `max_inflight` streams (1..64) take the batches: large requests stream 0,
+ * one after another (concurrent large sorts were measured slower: each one's
+ * partition output leaves L2 before its bucket phase reads it), batches of
+ * small requests the others; each holds several queued behind one another,
+ * so that the device never waits for the scheduler and work on different
+ * streams overlaps. */
 bitsort_status_t bitsort_server_create(int device, uint64_t budget_bytes, int max_inflight,
                                        bitsort_server_t **server);
 
 /* Queue one request (device pointers, caller-owned until it completes).
- * Returns BITSORT_ERR_BUDGET if the request alone exceeds the budget,
+ * Returns BITSORT_ERR_BUDGET if the request alone (with the scratch of its
+ * plain sort) exceeds the budget,
  * BITSORT_ERR_INVALID for bad arguments.  *ticket identifies it. */
 bitsort_status_t bitsort_server_submit(bitsort_server_t *server, const uint32_t *keys, uint64_t n,
                                        uint32_t max_value, uint32_t *out, uint64_t *ticket);

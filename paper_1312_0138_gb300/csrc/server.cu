@@ -4,7 +4,10 @@
 // A scheduler thread owns the device side:
 //   * requests wait in arrival order; the head request is admitted while the
 //     bytes its bitmap and output need, ceil(M/8) + 4n, fit in what is left of
-//     the budget (strict FIFO, so a large request is never starved);
+//     the budget after the admitted requests and the device memory the
+//     streams' contexts hold (for a large request, plus the growth of that
+//     memory its plain sort asks for); strict FIFO, so a large request is
+//     never starved;
 //   * admitted work is launched at once as batches: a request of at least
 //     kPlainMinKeys keys alone, as one plain sort (one kernel per phase,
 //     every SM), or else the run of smaller requests at the head, up to
@@ -83,6 +86,19 @@ uint64_t request_bytes(uint64_t n, uint32_t max_value) {
     const uint64_t M = (uint64_t)max_value + 1;
     return (M + 7) / 8 + 4 * n;
 }
+// Device memory a lane's context keeps between calls (its partition buffer
+// and global bitmap, at their high-water sizes).
+uint64_t lane_scratch(const bitsort_ctx *c) { return c->part_cap * 4 + c->bitmap_words * 4; }
+// The scratch a plain sort of (n, max_value) asks its context for.
+uint64_t plain_scratch(bitsort_ctx *c, uint64_t n, uint32_t max_value) {
+    const uint64_t M = (uint64_t)max_value + 1;
+    bsx_single_plan pl;
+    bsx_plan_single(c->sms, c->smem_optin, bsx_lookup_config(c, n, M), n, M, false, true, pl);
+    if (pl.cfg.path == BITSORT_PATH_PARTITION && pl.a.layout == bsx::LAYOUT_CAPACITY)
+        return (uint64_t)pl.a.nslices * pl.a.cap * 4;
+    if (pl.cfg.path == BITSORT_PATH_GLOBAL) return ((M + 31) / 32 + 3) / 4 * 16;
+    return 0;
+}
 
 }  // namespace
 
@@ -90,6 +106,7 @@ struct bitsort_server {
     int device = 0;
     uint64_t budget = 0;
     uint64_t in_use = 0;
+    uint64_t held = 0;     // device memory the lanes' contexts keep (counted against the budget)
     bitsort_ctx *ctx = nullptr;
     std::vector<Lane> lanes;
     std::vector<Batch> pool;
@@ -218,7 +235,15 @@ void bitsort_server::run() {
                 Request &r = reqs[waiting.front()];
                 const bool large = r.n >= kPlainMinKeys;
                 if (large && !batch.empty()) break;
-                if (in_use + r.bytes > budget) break;
+                // a plain sort may grow its lane's buffers, which then stay
+                // held: that growth is charged too
+                uint64_t growth = 0;
+                if (large) {
+                    const uint64_t need = plain_scratch(lanes[lane].ctx, r.n, r.max_value);
+                    const uint64_t have = lane_scratch(lanes[lane].ctx);
+                    growth = need > have ? need - have : 0;
+                }
+                if (in_use + held + growth + r.bytes > budget) break;
                 in_use += r.bytes;
                 batch.push_back(waiting.front());
                 waiting.pop_front();
@@ -243,6 +268,8 @@ void bitsort_server::run() {
             const uint32_t before = lanes[lane].queued;
             const bool ok = launch_batch(*b, jobs);
             lk.lock();
+            held = 0;
+            for (const Lane &ln : lanes) held += lane_scratch(ln.ctx);
             ++batches;
             if (!ok) {
                 fatal = BITSORT_ERR_CUDA;
@@ -328,6 +355,7 @@ extern "C" bitsort_status_t bitsort_server_submit(bitsort_server_t *sv, const ui
     if (st != BITSORT_OK) return st;
     const uint64_t bytes = request_bytes(n, max_value);
     if (bytes > sv->budget) return BITSORT_ERR_BUDGET;
+    if (n >= kPlainMinKeys && bytes + plain_scratch(sv->ctx, n, max_value) > sv->budget) return BITSORT_ERR_BUDGET;
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) return BITSORT_ERR_INVALID;
     const uint64_t t = sv->next_ticket++;
