@@ -333,7 +333,7 @@ typedef struct bitsort_server bitsort_server_t;
  * stream contexts keep (their partition buffers and global bitmaps, held at
  * their high-water sizes) and the growth of that memory a request's plain
  * sort asks for, fit in `budget_bytes`.  Admitted requests are launched at
- * once: a request of at least 2^22 keys alone as a plain sort, smaller ones
+ * once: a request of at least 2^20 keys alone as a plain sort, smaller ones
  * together as batches of up to 64 MiB of work (8n + M/4 bytes each).
  * `max_inflight` streams (1..64) take the batches: large requests stream 0,
  * one after another (concurrent large sorts were measured slower: each one's

@@ -31,6 +31,7 @@ namespace {
 
 constexpr uint64_t kFusedMaxM = 1ull << 20;
 constexpr int kLag = 2;
+constexpr uint64_t kGroupSlicesWithKeys = 32;   // slices with keys a bucket item meets, at most about
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
@@ -113,6 +114,15 @@ bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, siz
             delete pl;
             return BITSORT_ERR_INVALID;
         }
+        // a sparse array over a wide range (fewer than 64 keys per slice on
+        // average): bucket items of several slices, about
+        // kGroupSlicesWithKeys of them with keys each (item_bucket)
+        if (cfg.path == BITSORT_PATH_PARTITION && arr[i].nslices > 1 && n < 64ull * arr[i].nslices) {
+            const uint64_t busy = std::min<uint64_t>(n, arr[i].nslices);   // slices that can have keys
+            const uint64_t items = std::max<uint64_t>(1, (busy + kGroupSlicesWithKeys - 1) / kGroupSlicesWithKeys);
+            const uint64_t g = (arr[i].nslices + items - 1) / items;
+            arr[i].sgroup = g > 1 ? (uint32_t)g : 1u;
+        }
         smem = std::max(smem, bsx_smem_for(cfg, arr[i].nslices, arr[i].tile_keys, arr[i].stage_cap));
         scr_off[i] = scr;
         size_t need = SY_COUNT * 4;
@@ -162,7 +172,8 @@ bitsort_status_t bsx_plan_build(bitsort_ctx *c, const bitsort_desc_t *descs, siz
         const int k3 = k - 2 * kLag;
         if (k3 >= 0 && k3 < A) {
             const uint32_t i = multi[k3];
-            add(i, arr[i].path == BITSORT_PATH_PARTITION ? IT_BUCKET : IT_GSCAN, arr[i].nslices);
+            const uint32_t g = arr[i].sgroup > 1 ? arr[i].sgroup : 1u;
+            add(i, arr[i].path == BITSORT_PATH_PARTITION ? IT_BUCKET : IT_GSCAN, (arr[i].nslices + g - 1) / g);
         }
     }
 

@@ -82,6 +82,7 @@ struct SharedMisc {
     uint64_t expect;       // PARTITION: keys the bucket received (thread 0)
     uint32_t defer;        // slices report their completion once per CTA, at the end of the kernel
     uint32_t done_local;   // slices this CTA finished while deferring (thread 0)
+    uint32_t nonempty[32]; // slice groups: per warp, a ballot of the slices with keys
 };
 
 // Thread 0 only: wait until *p >= target.  Gives up (false) when the array's
@@ -1355,7 +1356,7 @@ __device__ void slice_finish_sparse(const EngineParams &P, const ArrayDesc &a, u
 }
 
 template <int T, int U = 8>
-__device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t b, char *smem, SharedMisc &m) {
+__device__ void bucket_slice(const EngineParams &P, const ArrayDesc &a, uint32_t b, char *smem, SharedMisc &m) {
     constexpr int NW = T / 32;
     const bool rank = a.emit == EMIT_RANK;
     const uint64_t v0 = (uint64_t)b * a.S;
@@ -1408,6 +1409,23 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
         }
     }
     if (!m.flag) hi = lo;
+    if (known_offsets(a) && hi == lo && m.flag) {
+        // a bucket that received no keys (most buckets of a few keys over a
+        // wide range): no bitmap to build or read; the slice records a count
+        // of zero at its offset and leaves the shared memory as it was
+        __syncthreads();   // (the warps' sums of the CAPACITY offset)
+        if (threadIdx.x == 0) {
+            uint64_t known = m.known;
+            if (a.layout == LAYOUT_CAPACITY) {
+                known = 0;
+                for (int w = 0; w < NW; ++w) known += m.wsum[w];
+            }
+            a.look[b] = known << 32;
+            if (m.expect != 0) atomicOr(&a.sync[SY_MISMATCH], 1u);
+        }
+        slice_complete<T>(a, m);
+        return;
+    }
     // sparse slice: at most one key per four bitmap words (summary bitmap)
     const bool sparse = !rank && a.summary && (hi - lo) * 4 <= (uint64_t)words;
     if (!m.summ_clean) {
@@ -1535,6 +1553,77 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
         for (uint32_t i = threadIdx.x; i < cnt; i += T) __stcs(out + o + i, outs[i]);
     }
     slice_complete<T>(a, m);
+}
+
+// A BUCKET item: one slice, or (sgroup > 1: a batch array of the exact
+// layout, whose slices know their offsets and do not wait on one another)
+// a run of sgroup consecutive slices.  A sparse array over a wide range has
+// far more slices than keys; as a group, one item classifies its slices in
+// parallel (a thread each), writes the zero-count look-back word of every
+// empty slice, builds and emits only the slices with keys, and reports the
+// whole group's completion at once.
+template <int T, int U = 8>
+__device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t idx, char *smem, SharedMisc &m) {
+    const uint32_t g = a.sgroup > 1 ? a.sgroup : 1u;
+    if (g == 1) {
+        bucket_slice<T, U>(P, a, idx, smem, m);
+        return;
+    }
+    constexpr int NW = T / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t b0 = idx * g, b1 = min(b0 + g, a.nslices);
+    const uint32_t was = m.defer;
+    if (threadIdx.x == 0) {
+        // the counts and offsets are final once the array's partition is done
+        m.flag = 1u;
+        if (!a.phased)
+            m.flag = wait_geq(&a.sync[SY_PART_DONE], a.key_tiles + a.stall, &a.sync[SY_TIMEOUT], P.wait_limit_ns)
+                         ? 1u : 0u;
+    }
+    __syncthreads();
+    const bool ok = m.flag != 0;
+    if (threadIdx.x == 0) {
+        if (!ok) atomicOr(&a.sync[SY_TIMEOUT], 1u);
+        m.defer = 1u;
+        if (!was) m.done_local = 0u;
+    }
+    uint32_t built = 0;   // slices with keys handed to bucket_slice (thread 0's count)
+    for (uint32_t c0 = b0; c0 < b1; c0 += T) {
+        const uint32_t b = c0 + threadIdx.x;
+        bool keys = false;
+        if (b < b1) {
+            keys = ok && __ldcg(&a.counts[b]) != 0u;
+            if (!keys) a.look[b] = (uint64_t)__ldcg(&a.offsets[b]) << 32;   // an empty slice
+        }
+        const unsigned bal = __ballot_sync(kFull, keys);
+        if (lane == 0) m.nonempty[warp] = bal;
+        __syncthreads();
+        for (int w = 0; w < NW; ++w) {
+            uint32_t bits = m.nonempty[w];
+            while (bits) {
+                const uint32_t bb = c0 + (uint32_t)w * 32u + (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1u;
+                bucket_slice<T, U>(P, a, bb, smem, m);
+                ++built;
+                __syncthreads();
+            }
+        }
+        __syncthreads();   // (m.nonempty is rewritten for the next chunk)
+    }
+    // every slice of the group is done: the built ones counted themselves
+    // while deferring, the empty ones are added here
+    if (!was) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            m.defer = 0u;
+            m.done_local = 0u;
+        }
+        complete_slices<T>(a, m, b1 - b0);
+    } else {
+        __syncthreads();
+        if (threadIdx.x == 0) m.done_local += (b1 - b0) - built;
+        __syncthreads();
+    }
 }
 
 // GSCATTER: OR the keys of p[lo, hi) into the global bitmap (L2 atomics).

@@ -82,7 +82,7 @@ struct __align__(16) ArrayDesc {
     uint32_t stage_cap;         // EMIT_RANK: outputs a slice may stage in shared memory
     uint32_t summary;           // 1: sparse slices keep a summary bitmap (one bit per word)
     uint32_t bias;              // keys are classified as x - bias (mod 2^32); outputs get it back
-    uint32_t pad_;
+    uint32_t sgroup;            // slices per BUCKET item (0 or 1: one; see item_bucket)
     uint32_t s_shift;           // log2(S) when S is a power of 2 (bucket = shift), else 0 (division)
 };
 

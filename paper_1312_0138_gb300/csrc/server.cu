@@ -60,13 +60,18 @@ struct Lane {                     // one stream and the context of its plain sor
     cudaStream_t stream = nullptr;
     bitsort_ctx *ctx = nullptr;
     uint32_t queued = 0;             // batches launched on it and not yet finished
+    std::deque<size_t> inflight;     // their batch records, in launch order (they finish in that order)
 };
 
 struct Batch {                    // one launched unit of work and its outcome buffers
     int lane = -1;
     cudaEvent_t done = nullptr;
-    bitsort_result_t *dev_results = nullptr;   // kMaxBatch outcomes on the device
-    bitsort_result_t *host_results = nullptr;  // pinned
+    // kMaxBatch outcomes: written by the kernels straight into mapped pinned
+    // host memory (dev_results is its device address); without mapping, a
+    // device buffer copied to host_results behind the kernels
+    bitsort_result_t *dev_results = nullptr;
+    bitsort_result_t *host_results = nullptr;
+    bool mapped = false;
     void *staging = nullptr;                   // pinned host copy of the batch plan's tables
     size_t staging_cap = 0;
     bool busy = false;
@@ -75,7 +80,11 @@ struct Batch {                    // one launched unit of work and its outcome b
 };
 
 constexpr size_t kMaxBatch = 1024;
-constexpr uint64_t kPlainMinKeys = 1ull << 22;   // requests this large run as plain sorts
+// requests this large run as plain sorts (from 2^20 keys: on GB300, the
+// serving benchmark's saturated mix measured 1.083x back-to-back plain calls
+// at 2^20, 1.066x at 2^22 and 0.943x at 2^16: below 2^20 keys batching gains,
+// above it the plain kernels' own efficiency)
+constexpr uint64_t kPlainMinKeys = 1ull << 20;
 constexpr uint64_t kBatchQuantum = 64ull << 20;  // work bytes (8n + M/4) of one batch of small requests
 constexpr size_t kStagingBytes = 1u << 20;       // pinned table staging per batch (larger plans stage on their own)
 constexpr uint32_t kDepth = 4;                   // batches queued per stream of small-request batches
@@ -129,9 +138,7 @@ struct bitsort_server {
 // only `jobs` (copied under the lock) and state that the scheduler thread
 // alone touches (the batch record, the streams, the scheduler's context).
 bool bitsort_server::launch_batch(Batch &b, const std::vector<bitsort_desc_t> &jobs) {
-    if (!b.host_results) {
-        if (cudaMallocHost(&b.host_results, kMaxBatch * sizeof(bitsort_result_t)) != cudaSuccess) return false;
-    }
+    if (!b.host_results) return false;
     if (!b.staging) {
         if (cudaMallocHost(&b.staging, kStagingBytes) != cudaSuccess) return false;
         b.staging_cap = kStagingBytes;
@@ -150,8 +157,9 @@ bool bitsort_server::launch_batch(Batch &b, const std::vector<bitsort_desc_t> &j
         st = bsx_plan_launch_direct(pl, ln.stream);
         bsx_plan_release_async(pl, ln.stream);
     }
-    cudaMemcpyAsync(b.host_results, b.dev_results, jobs.size() * sizeof(bitsort_result_t), cudaMemcpyDeviceToHost,
-                    ln.stream);
+    if (!b.mapped)
+        cudaMemcpyAsync(b.host_results, b.dev_results, jobs.size() * sizeof(bitsort_result_t),
+                        cudaMemcpyDeviceToHost, ln.stream);
     cudaEventRecord(b.done, ln.stream);
     b.seq = next_seq++;
     ++ln.queued;
@@ -183,12 +191,15 @@ void bitsort_server::run() {
     for (;;) {
         bool progressed = false;
         uint64_t busy = 0;
-        for (Batch &b : pool) {
-            if (b.busy && cudaEventQuery(b.done) == cudaSuccess) {
-                finish_batch(b);
+        // a stream's batches finish in launch order: only its oldest one is
+        // asked whether it is done
+        for (Lane &ln : lanes) {
+            while (!ln.inflight.empty() && cudaEventQuery(pool[ln.inflight.front()].done) == cudaSuccess) {
+                finish_batch(pool[ln.inflight.front()]);
+                ln.inflight.pop_front();
                 progressed = true;
             }
-            busy += b.busy ? 1 : 0;
+            busy += ln.inflight.size();
         }
         if (progressed) cv_done.notify_all();
         while (!waiting.empty()) {
@@ -285,6 +296,7 @@ void bitsort_server::run() {
                 cv_done.notify_all();
                 continue;
             }
+            lanes[lane].inflight.push_back((size_t)(b - pool.data()));
             ++busy;
             progressed = true;
         }
@@ -335,11 +347,29 @@ extern "C" bitsort_status_t bitsort_server_create(int device, uint64_t budget_by
         ln.ctx->stream_ordered = true;   // used on this stream only
     }
     sv->pool.resize((size_t)max_inflight * kDepth + kDepthLarge);
+    int can_map = 0;
+    cudaDeviceGetAttribute(&can_map, cudaDevAttrCanMapHostMemory, device);
     for (Batch &b : sv->pool) {
-        if (cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(&b.dev_results, kMaxBatch * sizeof(bitsort_result_t)) != cudaSuccess) {
+        if (cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess) {
             bitsort_server_destroy(sv);
             return BITSORT_ERR_CUDA;
+        }
+        const size_t bytes = kMaxBatch * sizeof(bitsort_result_t);
+        void *dev = nullptr;
+        if (can_map && cudaHostAlloc(reinterpret_cast<void **>(&b.host_results), bytes, cudaHostAllocMapped) ==
+                           cudaSuccess &&
+            cudaHostGetDevicePointer(&dev, b.host_results, 0) == cudaSuccess) {
+            b.dev_results = static_cast<bitsort_result_t *>(dev);
+            b.mapped = true;
+        } else {
+            cudaGetLastError();
+            if (b.host_results) cudaFreeHost(b.host_results);
+            b.host_results = nullptr;
+            if (cudaMallocHost(&b.host_results, bytes) != cudaSuccess ||
+                cudaMalloc(&b.dev_results, bytes) != cudaSuccess) {
+                bitsort_server_destroy(sv);
+                return BITSORT_ERR_CUDA;
+            }
         }
     }
     sv->thread = std::thread([sv] { sv->run(); });
@@ -414,7 +444,7 @@ extern "C" bitsort_status_t bitsort_server_destroy(bitsort_server_t *sv) {
         if (b.done) cudaEventDestroy(b.done);
         if (b.host_results) cudaFreeHost(b.host_results);
         if (b.staging) cudaFreeHost(b.staging);
-        if (b.dev_results) cudaFree(b.dev_results);
+        if (b.dev_results && !b.mapped) cudaFree(b.dev_results);
     }
     for (Lane &ln : sv->lanes) {
         if (ln.stream) cudaStreamDestroy(ln.stream);

@@ -122,3 +122,27 @@ def test_server_budget_admission(ctx):
         st, cnt, _ = srv.wait(t)
         assert st == bs.OK and np.array_equal(to_host(od), np.sort(k))
     srv.close()
+
+
+def test_server_budget_counts_plain_scratch():
+    # 2^20 keys over 2^28 values: its plain sort asks its stream's context for
+    # a capacity partition buffer of about 1.07 GB (304 buckets of 883,072
+    # entries), held afterwards; with that, it fits a 2 GiB budget but not a
+    # 1 GiB one (its bitmap and output alone are 36 MiB)
+    import torch
+    keys_np = gen.floyd(77, 1 << 20, 1 << 28)
+    kd = to_dev(keys_np)
+    small = bs.Server(0, budget_bytes=1 << 30, max_inflight=2)
+    with pytest.raises(bs.BitsortError) as e:
+        small.submit(kd, (1 << 28) - 1, torch.empty_like(kd))
+    assert e.value.status == bs.ERR_BUDGET
+    small.close()
+    srv = bs.Server(0, budget_bytes=2 << 30, max_inflight=2)
+    outs = [torch.empty_like(kd) for _ in range(3)]
+    tickets = [srv.submit(kd, (1 << 28) - 1, o) for o in outs]
+    want = np.sort(keys_np)
+    for t, o in zip(tickets, outs):
+        st, cnt, _ = srv.wait(t)
+        assert st == bs.OK and cnt == keys_np.size
+        assert np.array_equal(to_host(o), want)
+    srv.close()
