@@ -1562,13 +1562,12 @@ __device__ void bucket_slice(const EngineParams &P, const ArrayDesc &a, uint32_t
 // parallel (a thread each), writes the zero-count look-back word of every
 // empty slice, builds and emits only the slices with keys, and reports the
 // whole group's completion at once.
-template <int T, int U = 8>
-__device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t idx, char *smem, SharedMisc &m) {
-    const uint32_t g = a.sgroup > 1 ? a.sgroup : 1u;
-    if (g == 1) {
-        bucket_slice<T, U>(P, a, idx, smem, m);
-        return;
-    }
+// (compiled on its own, not inlined: its copy of the slice code then does
+// not weigh on the register allocation of the one-slice path)
+template <int T, int U>
+__device__ __noinline__ void bucket_group(const EngineParams &P, const ArrayDesc &a, uint32_t idx, char *smem,
+                                          SharedMisc &m) {
+    const uint32_t g = a.sgroup;
     constexpr int NW = T / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t b0 = idx * g, b1 = min(b0 + g, a.nslices);
@@ -1624,6 +1623,13 @@ __device__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t 
         if (threadIdx.x == 0) m.done_local += (b1 - b0) - built;
         __syncthreads();
     }
+}
+
+template <int T, int U = 8>
+__device__ __forceinline__ void item_bucket(const EngineParams &P, const ArrayDesc &a, uint32_t idx, char *smem,
+                                            SharedMisc &m) {
+    if (a.sgroup > 1) bucket_group<T, U>(P, a, idx, smem, m);
+    else bucket_slice<T, U>(P, a, idx, smem, m);
 }
 
 // GSCATTER: OR the keys of p[lo, hi) into the global bitmap (L2 atomics).
