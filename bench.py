@@ -248,7 +248,8 @@ def run_plain(args, w, ws, rank, local):
     if args.path:
         ctx.set_config(n, M - 1, {"fused": 1, "partition": 2, "global": 3}[args.path], args.slice, args.threads,
                        words_per_lane=args.wpl, stage=args.stage, layout=args.layout, persistent=args.persistent,
-                       emit=args.emit, part_stream=args.part_stream, part_threads=args.part_threads)
+                       emit=args.emit, part_stream=args.part_stream, part_threads=args.part_threads,
+                       part_tile_keys=args.part_tile_keys)
     cfg = ctx.get_config(n, M - 1)
     flush = L2Flush(args.flush)
     stream = torch.cuda.current_stream()
@@ -306,13 +307,13 @@ def run_plain(args, w, ws, rank, local):
     # algorithmic bytes of one launch of each kernel: 8 B per key (read + write
     # of a 4-byte key) and, for the kernels that build and read the bitmap,
     # M/8 + M/8 bitmap bytes
-    kernel_bytes = {"hist": 4 * n, "part": 8 * n, "parts": 8 * n, "gscatter": 4 * n + M // 8, "gscan": 4 * n + M // 8,
-                    "bucket": 8 * n + M // 4, "persistent": 8 * n + M // 4}
+    kernel_bytes = {"hist": 4 * n, "part": 8 * n, "parts": 8 * n, "partw": 8 * n, "gscatter": 4 * n + M // 8,
+                    "gscan": 4 * n + M // 8, "bucket": 8 * n + M // 4, "persistent": 8 * n + M // 4}
     # the bytes each kernel must move through L2 / HBM: the bucket kernel
     # builds and reads its bitmap slices in shared memory (M/4 never leaves
     # the SM; sparse slices skip most of it through the summary bitmap), the
     # global-bitmap kernels really move their bitmap bytes through L2
-    kernel_hbm_bytes = {"hist": 4 * n, "part": 8 * n, "parts": 8 * n, "gscatter": 4 * n + M // 8,
+    kernel_hbm_bytes = {"hist": 4 * n, "part": 8 * n, "parts": 8 * n, "partw": 8 * n, "gscatter": 4 * n + M // 8,
                         "gscan": 4 * n + M // 8, "bucket": 8 * n, "persistent": 8 * n}
     dom_bytes = kernel_bytes.get(dom, algo_bytes)
     dom_hbm_bytes = kernel_hbm_bytes.get(dom, 8 * n)
@@ -686,6 +687,7 @@ def main():
     ap.add_argument("--emit", type=int, default=0)
     ap.add_argument("--part-stream", type=int, default=0)
     ap.add_argument("--part-threads", type=int, default=0)
+    ap.add_argument("--part-tile-keys", type=int, default=0)
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cub", action="store_true")

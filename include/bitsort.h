@@ -405,6 +405,13 @@ typedef enum {
  *   part_threads    block size of the histogram and partition phases of a
  *                   one-kernel-per-phase plan (256, 512 or 1024); 0 = the
  *                   built-in rule (512 threads, 1024 from 1024 buckets).
+ *   part_tile_keys  keys per partition tile when that phase runs at 1024
+ *                   threads and its tiles are not streamed: 16384, or 32768
+ *                   (wide tiles: a counting sort per tile, with the next
+ *                   tile copied in while the current one is written out);
+ *                   0 = the built-in rule (32768 when the shared memory
+ *                   holds such a tile and there are at least eight tiles
+ *                   per SM, else 16384).  Other values count as 0.
  *   ms              measured time when tuned (output only). */
 typedef struct {
     int32_t path;
@@ -418,7 +425,7 @@ typedef struct {
     uint32_t part_stream;
     uint32_t summary;
     uint32_t part_threads;
-    uint32_t reserved;
+    uint32_t part_tile_keys;
     double ms;
 } bitsort_config_t;
 
@@ -506,7 +513,9 @@ bitsort_status_t bitsort_debug_stalled_launch(bitsort_ctx_t *ctx, const uint32_t
  * event and writes the last call's kernel durations in milliseconds to
  * ms[0..*count) in launch order, with each kernel's item type in kinds[]
  * (0 histogram, 1 partition, 2 bucket slices, 3 global scatter, 4 global
- * scan, -1 persistent); both arrays need room for 8 entries. */
+ * scan, 5 partition streamed through bulk copies, 6 partition in wide
+ * tiles, 16 multiset histogram, 17 multiset split, -1 persistent); both
+ * arrays need room for 8 entries. */
 bitsort_status_t bitsort_set_phase_timing(bitsort_ctx_t *ctx, int enable);
 bitsort_status_t bitsort_phase_times(bitsort_ctx_t *ctx, float *ms, int *kinds, int *count);
 

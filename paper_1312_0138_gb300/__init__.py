@@ -67,15 +67,16 @@ class Config(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("slice_values", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("words_per_lane", ctypes.c_uint32), ("stage", ctypes.c_uint32), ("layout", ctypes.c_uint32),
                 ("persistent", ctypes.c_uint32), ("emit", ctypes.c_uint32), ("part_stream", ctypes.c_uint32),
-                ("summary", ctypes.c_uint32), ("part_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("ms", ctypes.c_double)]
+                ("summary", ctypes.c_uint32), ("part_threads", ctypes.c_uint32),
+                ("part_tile_keys", ctypes.c_uint32), ("ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"path": PATH_NAMES.get(self.path, self.path), "slice_values": self.slice_values,
                 "threads": self.block_threads, "words_per_lane": self.words_per_lane, "stage": self.stage,
                 "layout": LAYOUT_NAMES.get(self.layout, self.layout), "persistent": self.persistent,
                 "emit": EMIT_NAMES.get(self.emit, self.emit), "part_stream": self.part_stream,
-                "summary": self.summary, "part_threads": self.part_threads, "ms": self.ms}
+                "summary": self.summary, "part_threads": self.part_threads,
+                "part_tile_keys": self.part_tile_keys, "ms": self.ms}
 
 
 LAYOUT_EXACT, LAYOUT_CAPACITY = 0, 1
@@ -371,9 +372,10 @@ class Context:
     # tuning ----------------------------------------------------------------
     def set_config(self, n: int, max_value: int, path: int, slice_values: int = 0, threads: int = 0,
                    words_per_lane: int = 0, stage: int = 0, layout: int = LAYOUT_CAPACITY, persistent: int = 0,
-                   emit: int = EMIT_WORD, part_stream: int = 0, summary: int = 1, part_threads: int = 0):
+                   emit: int = EMIT_WORD, part_stream: int = 0, summary: int = 1, part_threads: int = 0,
+                   part_tile_keys: int = 0):
         cfg = Config(path, slice_values, threads, words_per_lane, stage, layout, persistent, emit, part_stream,
-                     summary, part_threads, 0, 0.0)
+                     summary, part_threads, part_tile_keys, 0.0)
         _check(load().bitsort_set_config(self.handle, n, max_value, ctypes.byref(cfg)), "bitsort_set_config")
 
     def get_config(self, n: int, max_value: int):
@@ -413,7 +415,7 @@ class Context:
         cnt = ctypes.c_int(0)
         _check(load().bitsort_phase_times(self.handle, ms, kinds, ctypes.byref(cnt)), "bitsort_phase_times")
         names = {-1: "persistent", 0: "hist", 1: "part", 2: "bucket", 3: "gscatter", 4: "gscan", 5: "parts",
-                 6: "mhist", 7: "msplit"}
+                 6: "partw", 16: "mhist", 17: "msplit"}
         return [(names.get(kinds[i], kinds[i]), ms[i]) for i in range(cnt.value)]
 
     def kernel_launches(self) -> int:

@@ -262,6 +262,7 @@ bsx_config bsx_sanitize(bsx_config cfg, uint64_t n, uint64_t M) {
     if (cfg.threads == 1024 && cfg.persistent) cfg.threads = 512;   // the persistent engine has 256 / 512
     if (cfg.part_threads != 0 && cfg.part_threads != 256 && cfg.part_threads != 512 && cfg.part_threads != 1024)
         cfg.part_threads = 0;
+    if (cfg.part_tile_keys != 16384u && cfg.part_tile_keys != 32768u) cfg.part_tile_keys = 0;
     if (cfg.wpl != 1 && cfg.wpl != 2 && cfg.wpl != 4 && cfg.wpl != 8) cfg.wpl = 2;
     if (cfg.stage && cfg.wpl == 2) cfg.wpl = 1;    // staged emission: 1, 4 or 8 words per lane
     if (!cfg.stage && cfg.wpl == 8) cfg.wpl = 4;   // direct emission: 1, 2 or 4
@@ -480,6 +481,20 @@ void bsx_plan_single(int sms, uint32_t smem_optin, const bsx_config &cfg0, uint6
         a.tile_keys = (uint32_t)(kKeysPerThread * Tp);
         a.key_tiles = (uint32_t)ceil_div(n, (uint64_t)a.tile_keys);
     }
+    // wide partition tiles at 1024 threads: where the shared memory holds
+    // one and the array gives every SM at least eight of them (fewer tiles
+    // than that leave SMs idle at the end), or where the configuration asks
+    pl.wide_part = false;
+    if (!cfg.persistent && partitioned && !pl.stream_part && Tp == 1024) {
+        const uint32_t wk = (uint32_t)(kWideKeysPerThread * 1024);
+        const bool fits = part_phase_smem_bytes(a.nslices, wk) <= smem_optin;
+        const bool many = ceil_div(n, (uint64_t)wk) >= 8ull * (uint64_t)sms;
+        if (fits && (cfg.part_tile_keys == 32768u || (cfg.part_tile_keys == 0 && many))) {
+            pl.wide_part = true;
+            a.tile_keys = wk;
+            a.key_tiles = (uint32_t)ceil_div(n, (uint64_t)wk);
+        }
+    }
     pl.cfg = cfg;
     pl.Tp = Tp;
     pl.Tb = Tb;
@@ -576,7 +591,8 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
     const int Tp = pl.Tp, Tb = pl.Tb;
     int launched = 0;
     auto phase = [&](int kind, uint32_t items, uint32_t smem) -> bool {
-        const int Tk = (kind == IT_HIST || kind == IT_PART || kind == IT_PARTS) ? Tp : kind == IT_BUCKET ? Tb : T;
+        const int Tk = (kind == IT_HIST || kind == IT_PART || kind == IT_PARTS || kind == IT_PARTW) ? Tp
+                       : kind == IT_BUCKET ? Tb : T;
         if (items == 0) return true;
         if (smem > c->smem_optin) {
             bsx_note_error((int)cudaErrorInvalidValue, "shared memory above the per-block limit");
@@ -592,7 +608,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         if (kernel_max_blocks_per_sm(kind, Tk, smem, &per_sm) != 0 || per_sm < 1) per_sm = 1;
         // slice phases and the streaming HIST / GSCATTER / PARTS
         // phases: one wave of resident CTAs; PART: a few tiles per CTA
-        const bool one_wave = kind != IT_PART;
+        const bool one_wave = kind != IT_PART && kind != IT_PARTW;
         uint64_t grid = (uint64_t)c->sms * (uint64_t)per_sm * (one_wave ? 1u : 8u);
         if (grid > items) grid = items;
         int e = kernel_launch(kind, q, Tk, smem, (int)grid, stream, launched > 0);
@@ -613,7 +629,7 @@ static bitsort_status_t launch_single(bitsort_ctx *c, const bsx_config &cfg0, co
         ok = phase(IT_BUCKET, 1, sl);
     } else if (a.path == BITSORT_PATH_PARTITION) {
         // tiles of 16-byte aligned keys may stream through bulk copies
-        const int pk = pl.stream_part ? (int)IT_PARTS : (int)IT_PART;
+        const int pk = pl.stream_part ? (int)IT_PARTS : pl.wide_part ? (int)IT_PARTW : (int)IT_PART;
         if (a.layout == LAYOUT_EXACT) ok = phase(IT_HIST, a.key_tiles, pl.hist_smem);
         ok = ok && phase(pk, a.key_tiles, pl.part_smem) && phase(IT_BUCKET, a.nslices, sl);
     } else {
@@ -828,7 +844,7 @@ static void to_public(const bsx_config &c, bitsort_config_t *o) {
     o->part_stream = c.stream_part ? 1 : 0;
     o->summary = c.summary ? 1 : 0;
     o->part_threads = (uint32_t)c.part_threads;
-    o->reserved = 0;
+    o->part_tile_keys = c.part_tile_keys;
     o->ms = c.ms;
 }
 
@@ -856,6 +872,7 @@ extern "C" bitsort_status_t bitsort_set_config(bitsort_ctx_t *c, uint64_t n, uin
     cfg.stream_part = in->part_stream != 0;
     cfg.summary = in->summary != 0;
     cfg.part_threads = (int)in->part_threads;
+    cfg.part_tile_keys = in->part_tile_keys;
     c->table[key] = bsx_sanitize(cfg, n, M);
     return BITSORT_OK;
 }
@@ -963,6 +980,11 @@ std::vector<bsx_config> bsx_candidates(const bitsort_ctx *c, uint64_t n, uint64_
         for (int pt : {512, 1024}) {
             bsx_config v = b;
             v.part_threads = pt;
+            if (pt == 1024) {   // and both tile sizes of that block size
+                v.part_tile_keys = 16384u;
+                out.push_back(v);
+                v.part_tile_keys = 32768u;
+            }
             out.push_back(v);
         }
     }
@@ -1054,17 +1076,17 @@ extern "C" bitsort_status_t bitsort_tune_save(bitsort_ctx_t *c, const char *path
     FILE *f = fopen(path, "w");
     if (!f) return BITSORT_ERR_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
-    fprintf(f, "{\"version\": 2, \"entries\": [");
+    fprintf(f, "{\"version\": 3, \"entries\": [");
     bool first = true;
     for (auto &kv : c->table) {
         const bsx_config &g = kv.second;
         fprintf(f,
                 "%s\n  {\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
                 "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"part_stream\": %d, "
-                "\"summary\": %d, \"part_threads\": %d, \"ms\": %.6f}",
+                "\"summary\": %d, \"part_threads\": %d, \"part_tile_keys\": %u, \"ms\": %.6f}",
                 first ? "" : ",", kv.first.first, kv.first.second, (int)g.path, g.S, g.threads, g.wpl,
                 g.stage ? 1 : 0, g.layout, g.persistent ? 1 : 0, g.emit, g.stream_part ? 1 : 0, g.summary ? 1 : 0,
-                g.part_threads, g.ms);
+                g.part_threads, g.part_tile_keys, g.ms);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -1086,15 +1108,22 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
     size_t pos = 0;
     while ((pos = text.find("{\"log2n\"", pos)) != std::string::npos) {
         int ln = 0, lm = 0, p = 0, th = 0, stage = 0, pers = 0, pstream = 0, summary = 1, pth = 0;
-        unsigned S = 0, wpl = 0, layout = 0, emit = 0;
+        unsigned S = 0, wpl = 0, layout = 0, emit = 0, ptk = 0;
         double ms = 0;
-        // version 2 entries carry part_threads; version 1 entries do not
+        // version 3 entries carry part_threads and part_tile_keys, version 2
+        // entries part_threads, version 1 entries neither
         const char *entry = text.c_str() + pos;
-        const int got2 = sscanf(entry,
+        const int got3 = sscanf(entry,
+                   "{\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
+                   "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"part_stream\": %d, "
+                   "\"summary\": %d, \"part_threads\": %d, \"part_tile_keys\": %u, \"ms\": %lf",
+                   &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &emit, &pstream, &summary, &pth, &ptk, &ms);
+        const int got2 = got3 == 15 ? 14 : sscanf(entry,
                    "{\"log2n\": %d, \"log2m\": %d, \"path\": %d, \"slice_values\": %u, \"threads\": %d, "
                    "\"wpl\": %u, \"stage\": %d, \"layout\": %u, \"persistent\": %d, \"emit\": %u, \"part_stream\": %d, "
                    "\"summary\": %d, \"part_threads\": %d, \"ms\": %lf",
                    &ln, &lm, &p, &S, &th, &wpl, &stage, &layout, &pers, &emit, &pstream, &summary, &pth, &ms);
+        if (got3 != 15) ptk = 0;
         if (got2 != 14) {
             pth = 0;
             if (sscanf(entry,
@@ -1118,6 +1147,7 @@ extern "C" bitsort_status_t bitsort_tune_load(bitsort_ctx_t *c, const char *path
         cfg.stream_part = pstream != 0;
         cfg.summary = summary != 0;
         cfg.part_threads = pth;
+        cfg.part_tile_keys = ptk;
         cfg.ms = ms;
         table[std::make_pair(ln, lm)] = cfg;
         ++pos;

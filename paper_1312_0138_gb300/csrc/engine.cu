@@ -963,6 +963,70 @@ __device__ __forceinline__ uint2 part_run(const ArrayDesc &a, uint32_t i, uint32
     return make_uint2(base + at - p, fit + p);
 }
 
+// Steps 2 and 3 of a partition tile, once the tile's counts are in hist
+// (all bins, the discard bin nb last): every thread reserves the runs of its
+// buckets [lo_bin, hi_bin) in the partition buffer (global atomics, issued
+// ahead of the scan when it owns at most kOwnEarly bins), the block scans
+// the counts into tile prefixes (hist[i] = keys of the bins before i in the
+// tile), and each bucket with keys gets its run words.  Ends with a barrier.
+template <int T, bool kCheck>
+__device__ __forceinline__ void part_scan_bins(const ArrayDesc &a, uint32_t *hist, const uint32_t *base, uint2 *run,
+                                               uint32_t lo_bin, uint32_t hi_bin, SharedMisc &m) {
+    constexpr int NW = T / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nb = a.nslices;
+    const bool capacity = a.layout == LAYOUT_CAPACITY;
+    const bool early = hi_bin - lo_bin <= (uint32_t)kOwnEarly;
+    uint32_t at[kOwnEarly];
+    uint32_t own = 0;
+    if (early) {
+#pragma unroll
+        for (int k = 0; k < kOwnEarly; ++k) {
+            const uint32_t i = lo_bin + k;
+            const uint32_t c = i < hi_bin ? hist[i] : 0u;
+            at[k] = c ? atomicAdd(&a.cursor[i], c) : 0u;
+            own += c;
+        }
+    } else {
+        for (uint32_t i = lo_bin; i < hi_bin; ++i) own += hist[i];
+    }
+    const uint32_t incl = warp_incl_scan_u32(own, lane);
+    if (lane == 31) m.wcount[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < NW ? m.wcount[lane] : 0u;
+        const uint32_t wi = warp_incl_scan_u32(w, lane);
+        if (lane < NW) m.wbase[lane] = wi - w;
+        if (kCheck && lane == 31) {   // the discard bin after every bucket
+            if (hist[nb]) run[nb] = make_uint2(0u, 0u);
+            hist[nb] = wi;
+        }
+    }
+    __syncthreads();
+
+    uint32_t p = m.wbase[warp] + incl - own;
+    if (early) {
+#pragma unroll
+        for (int k = 0; k < kOwnEarly; ++k) {
+            const uint32_t i = lo_bin + k;
+            if (i < hi_bin) {
+                const uint32_t c = hist[i];
+                hist[i] = p;
+                if (c) run[i] = part_run(a, i, c, p, at[k], base[i], capacity);
+                p += c;
+            }
+        }
+    } else {
+        for (uint32_t i = lo_bin; i < hi_bin; ++i) {
+            const uint32_t c = hist[i];
+            hist[i] = p;
+            if (c) run[i] = part_run(a, i, c, p, atomicAdd(&a.cursor[i], c), base[i], capacity);
+            p += c;
+        }
+    }
+    __syncthreads();
+}
+
 // Keys of tile t into x (element j*T + threadIdx.x in x[j]): 16-byte loads
 // for a whole tile of 16-byte aligned keys; returns the tile's key count.
 template <int T>
@@ -1000,8 +1064,6 @@ __device__ void part_tile_phase(const ArrayDesc &a, uint32_t (&x)[kKeysPerThread
                                 const uint32_t *base, uint2 *run, uint32_t *sorted, uint32_t lo_bin, uint32_t hi_bin,
                                 SharedMisc &m, uint32_t next) {
     constexpr int K = kKeysPerThread;
-    constexpr int NW = T / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nb = a.nslices;
     const uint32_t bias = a.bias, maxv = (uint32_t)(a.M - 1), sh = a.s_shift;
     const uint64_t magic = a.div_magic;
@@ -1026,57 +1088,8 @@ __device__ void part_tile_phase(const ArrayDesc &a, uint32_t (&x)[kKeysPerThread
         __syncthreads();   // (EXACT: the histogram pass reports keys above max_value)
     }
 
-    // 2. reservations of this thread's buckets, issued before the scan
-    const bool early = hi_bin - lo_bin <= (uint32_t)kOwnEarly;
-    uint32_t at[kOwnEarly];
-    uint32_t own = 0;
-    if (early) {
-#pragma unroll
-        for (int k = 0; k < kOwnEarly; ++k) {
-            const uint32_t i = lo_bin + k;
-            const uint32_t c = i < hi_bin ? hist[i] : 0u;
-            at[k] = c ? atomicAdd(&a.cursor[i], c) : 0u;
-            own += c;
-        }
-    } else {
-        for (uint32_t i = lo_bin; i < hi_bin; ++i) own += hist[i];
-    }
-    const uint32_t incl = warp_incl_scan_u32(own, lane);
-    if (lane == 31) m.wcount[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = lane < NW ? m.wcount[lane] : 0u;
-        const uint32_t wi = warp_incl_scan_u32(w, lane);
-        if (lane < NW) m.wbase[lane] = wi - w;
-        if (kCheck && lane == 31) {   // the discard bin after every bucket
-            if (hist[nb]) run[nb] = make_uint2(0u, 0u);
-            hist[nb] = wi;
-        }
-    }
-    __syncthreads();
-
-    // 3. tile prefix and run words of every bucket with keys
-    uint32_t p = m.wbase[warp] + incl - own;
-    if (early) {
-#pragma unroll
-        for (int k = 0; k < kOwnEarly; ++k) {
-            const uint32_t i = lo_bin + k;
-            if (i < hi_bin) {
-                const uint32_t c = hist[i];
-                hist[i] = p;
-                if (c) run[i] = part_run(a, i, c, p, at[k], base[i], capacity);
-                p += c;
-            }
-        }
-    } else {
-        for (uint32_t i = lo_bin; i < hi_bin; ++i) {
-            const uint32_t c = hist[i];
-            hist[i] = p;
-            if (c) run[i] = part_run(a, i, c, p, atomicAdd(&a.cursor[i], c), base[i], capacity);
-            p += c;
-        }
-    }
-    __syncthreads();
+    // 2., 3. reservations, tile prefixes and run words of the buckets
+    part_scan_bins<T, kCheck>(a, hist, base, run, lo_bin, hi_bin, m);
 
     // 4. reorder by bin, then each bin's keys leave in consecutive stores
 #pragma unroll
@@ -1296,6 +1309,203 @@ __device__ void part_stream(const EngineParams &P, const ArrayDesc &a, char *sme
 // non-empty words: a lane takes one summary word (32 bitmap words) per step.
 // Every word read is cleared behind (bitmap and summary), so the slice is zero
 // again for this CTA's next sparse slice without a full clear.
+// ------------------------------------------------- PART with wide tiles
+// The phase kernel's partition at 1024 threads and 32 keys a thread: tiles
+// of 32 Ki keys.  Against part_tile_phase's 16 Ki keys, the per-bucket work
+// of a tile (reservations, prefixes, run words) is spread over twice the
+// keys, and with thousands of buckets each run the tile leaves in the
+// partition buffer is twice as long (fewer, fuller L2 writes).  Keys and
+// their ranks would not both fit the registers, so the tile is a counting
+// sort: pass 1 counts the keys per bin, the prefixes and reservations
+// follow, and pass 2 takes each key's slot from its bin's running prefix
+// (a shared-memory atomic; the order of a bucket's keys inside its run is
+// arbitrary, and the bucket phase does not depend on it).  The next tile
+// arrives while this one leaves: the write-out goes in four chunks, and
+// behind each of the first three the matching quarter of the next tile is
+// copied into the freed part of the tile buffer (cp.async, 16 bytes a
+// thread); the last quarter comes into registers.
+
+// Tile offset of a thread's element j: 16-byte group j/4 of the thread's
+// eight, groups of the block interleaved (group g of thread i at g*T + i).
+template <int T>
+__device__ __forceinline__ uint32_t wide_elem(int j) {
+    return 4u * ((uint32_t)(j >> 2) * T + threadIdx.x) + (uint32_t)(j & 3);
+}
+
+// Elements [J0, J1) of the tile of nkeys keys at a.keys + lo into x (vec:
+// a whole tile of 16-byte aligned keys, read in 16-byte loads).
+template <int T, int J0, int J1>
+__device__ __forceinline__ void wide_load(const ArrayDesc &a, uint64_t lo, uint32_t nkeys, bool vec,
+                                          uint32_t (&x)[kWideKeysPerThread]) {
+    if (vec) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.keys + lo);
+#pragma unroll
+        for (int g = J0 / 4; g < J1 / 4; ++g) {
+            const uint4 q = __ldcs(src + g * T + threadIdx.x);
+            x[4 * g] = q.x; x[4 * g + 1] = q.y; x[4 * g + 2] = q.z; x[4 * g + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = J0; j < J1; ++j) {
+            const uint32_t e = wide_elem<T>(j);
+            x[j] = e < nkeys ? __ldcs(a.keys + lo + e) : 0u;
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// One wide tile: x[j] holds tile element wide_elem(j) (valid while below
+// nkeys; every element when kFull).  Bucket ownership, the discard bin and
+// the zeroed histogram at the end are as in part_tile_phase.  stage_next:
+// tile `next` is whole and its keys 16-byte aligned; its groups 0..5 are
+// then copied into this thread's slots of the tile buffer (to be read by
+// this thread after cp_async_wait_all) and its groups 6, 7 loaded into
+// x[24..31].  Ends with a barrier.
+template <int T, bool kShift, bool kCheck, bool kFull>
+__device__ __forceinline__ void part_tile_wide(const ArrayDesc &a, uint32_t (&x)[kWideKeysPerThread], uint32_t nkeys,
+                                               uint32_t *hist, const uint32_t *base, uint2 *run, uint32_t *sorted,
+                                               uint32_t lo_bin, uint32_t hi_bin, SharedMisc &m, uint32_t next,
+                                               bool stage_next) {
+    constexpr int K = kWideKeysPerThread;
+    static_assert(T * K / 8 / T == 4, "four write-out chunks of eight keys a thread");
+    const uint32_t nb = a.nslices;
+    const uint32_t bias = a.bias, maxv = (uint32_t)(a.M - 1), sh = a.s_shift;
+    const uint64_t magic = a.div_magic;
+    const bool capacity = a.layout == LAYOUT_CAPACITY;
+
+    // 1. counts per bin
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if (kFull || wide_elem<T>(j) < nkeys) {
+            const uint32_t b = part_bin<kShift, kCheck>(x[j], bias, maxv, sh, magic, nb);
+            if (kCheck) bad |= b == nb;
+            atomicAdd(&hist[b], 1u);
+        }
+    }
+    if (kCheck && capacity) {
+        bad = __syncthreads_or(bad);
+        if (bad && threadIdx.x == 0) atomicOr(&a.sync[SY_RANGE], 1u);
+    } else {
+        __syncthreads();   // (EXACT: the histogram pass reports keys above max_value)
+    }
+
+    // 2., 3. reservations, tile prefixes and run words of the buckets
+    part_scan_bins<T, kCheck>(a, hist, base, run, lo_bin, hi_bin, m);
+
+    // 4. every key to the next slot of its bin
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if (kFull || wide_elem<T>(j) < nkeys) {
+            const uint32_t b = part_bin<kShift, kCheck>(x[j], bias, maxv, sh, magic, nb);
+            sorted[atomicAdd(&hist[b], 1u)] = x[j];
+        }
+    }
+    __syncthreads();
+
+    // 5. write-out, chunk c = sorted[8cT, 8(c+1)T): eight keys a thread, their
+    // loads, then their run words, then their stores
+    const uint64_t nlo = (uint64_t)next * a.tile_keys;
+    if (stage_next) wide_load<T, 24, 32>(a, nlo, a.tile_keys, true, x);
+    uint32_t *part = a.part;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint32_t v[8];
+        uint2 f[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t i = (uint32_t)(8 * c + u) * T + threadIdx.x;
+            v[u] = (kFull || i < nkeys) ? sorted[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) f[u] = run[part_bin<kShift, kCheck>(v[u], bias, maxv, sh, magic, nb)];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t i = (uint32_t)(8 * c + u) * T + threadIdx.x;
+            if ((kFull || i < nkeys) && i < f[u].y) part[f[u].x + i] = v[u];
+        }
+        if (c < 3) {
+            __syncthreads();   // chunk c is read: the next tile's groups 2c, 2c+1 may land there
+            if (stage_next) {
+                const uint32_t *src = a.keys + nlo;
+#pragma unroll
+                for (int g = 2 * c; g < 2 * c + 2; ++g) {
+                    const uint32_t e = 4u * ((uint32_t)g * T + threadIdx.x);
+                    cp_async16(sorted + e, src + e);
+                }
+                cp_async_commit();
+            }
+        }
+    }
+    for (uint32_t i = lo_bin; i < hi_bin; ++i) hist[i] = 0u;
+    if (kCheck && threadIdx.x == 0) hist[nb] = 0u;
+    __syncthreads();
+}
+
+// PART phase with wide tiles (T = 1024, a.tile_keys = 32 * T): a CTA takes
+// tiles t, t + G, t + 2G, ...  Shared memory as part_phase.  A tile that is
+// not whole, or keys that are not 16-byte aligned, are loaded by the threads
+// at the start of the tile instead of behind the previous one.  Every copy
+// a thread issues is waited for by that thread before its next tile, so none
+// is in flight when the CTA exits.
+template <int T>
+__device__ void part_wide(const EngineParams &P, const ArrayDesc &a, char *smem, SharedMisc &m) {
+    constexpr int K = kWideKeysPerThread;
+    const uint32_t nb = a.nslices, nbins = nb + 1;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *base = hist + nbins;
+    uint2 *run = reinterpret_cast<uint2 *>(smem + ((nbins * 8u + 7u) & ~7u));
+    uint32_t *sorted = reinterpret_cast<uint32_t *>(run + nbins);
+    const uint32_t per = (nb + T - 1) / T;
+    const uint32_t lo_bin = min(nb, threadIdx.x * per), hi_bin = min(nb, lo_bin + per);
+    const bool capacity = a.layout == LAYOUT_CAPACITY;
+    for (uint32_t i = lo_bin; i < hi_bin; ++i) {
+        hist[i] = 0u;
+        base[i] = capacity ? (uint32_t)((uint64_t)i * a.cap) : (uint32_t)__ldcg(&a.offsets[i]);
+    }
+    if (threadIdx.x == 0) hist[nb] = 0u;
+    __syncthreads();
+    const bool shift = a.s_shift != 0;
+    const bool check = a.M != (1ull << 32);
+    const bool aligned = (reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0;
+    const uint32_t TK = a.tile_keys;
+    auto keys_of = [&](uint32_t t) { return (uint32_t)(min((uint64_t)(t + 1) * TK, a.n) - (uint64_t)t * TK); };
+    uint32_t t = blockIdx.x;
+    if (t >= a.key_tiles) return;
+    uint32_t x[K];
+    uint32_t nkeys = keys_of(t);
+    wide_load<T, 0, K>(a, (uint64_t)t * TK, nkeys, aligned && nkeys == TK, x);
+    bool staged = false;
+    while (t < a.key_tiles) {
+        const uint32_t next = t + gridDim.x;
+        const bool stage_next = next < a.key_tiles && aligned && keys_of(next) == TK;
+        if (staged) {   // groups 0..5 copied by this thread behind the previous tile
+            cp_async_wait_all();
+            const uint4 *st4 = reinterpret_cast<const uint4 *>(sorted);
+#pragma unroll
+            for (int g = 0; g < 6; ++g) {
+                const uint4 q = st4[g * T + threadIdx.x];
+                x[4 * g] = q.x; x[4 * g + 1] = q.y; x[4 * g + 2] = q.z; x[4 * g + 3] = q.w;
+            }
+        }
+        if (nkeys != TK) part_tile_wide<T, false, true, false>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next, stage_next);
+        else if (shift && check) part_tile_wide<T, true, true, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next, stage_next);
+        else if (shift) part_tile_wide<T, true, false, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next, stage_next);
+        else if (check) part_tile_wide<T, false, true, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next, stage_next);
+        else part_tile_wide<T, false, false, true>(a, x, nkeys, hist, base, run, sorted, lo_bin, hi_bin, m, next, stage_next);
+        t = next;
+        if (t >= a.key_tiles) break;
+        nkeys = keys_of(t);
+        if (!stage_next) wide_load<T, 0, K>(a, (uint64_t)t * TK, nkeys, aligned && nkeys == TK, x);
+        staged = stage_next;
+    }
+}
+
 template <int T>
 __device__ void slice_finish_sparse(const EngineParams &P, const ArrayDesc &a, uint32_t s, uint32_t *bm,
                                     uint32_t *summ, uint32_t words, uint32_t v0, SharedMisc &m) {
@@ -1815,6 +2025,9 @@ __global__ void __launch_bounds__(T, MINB) phase_kernel(const __grid_constant__ 
     } else if constexpr (TYPE == IT_PART) {
         part_phase<T>(P, a, smem, m);
         pdl_trigger();
+    } else if constexpr (TYPE == IT_PARTW) {
+        part_wide<T>(P, a, smem, m);
+        pdl_trigger();
     } else {
         // HIST / GSCATTER stream one contiguous chunk of keys per CTA (one
         // flush of the shared histogram, one completion count per CTA)
@@ -1883,6 +2096,7 @@ static KernelFn kernel_for(int kind, int threads, bool solo = false) {
             case IT_GSCATTER: return phase_kernel<1024, IT_GSCATTER>;
             case IT_GSCAN: return phase_kernel<1024, IT_GSCAN>;
             case IT_PARTS: return phase_kernel<1024, IT_PARTS>;
+            case IT_PARTW: return phase_kernel<1024, IT_PARTW>;
         }
     }
     return nullptr;
@@ -1896,8 +2110,10 @@ static KernelFn kernel_for_smem(int kind, int threads, uint32_t smem_bytes) {
 }
 
 int engine_set_smem_limit(int threads, uint32_t smem_bytes) {
-    for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN, (int)IT_PARTS}) {
+    for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN, (int)IT_PARTS,
+                     (int)IT_PARTW}) {
         if (kind == -1 && threads == 1024) continue;   // no persistent engine at 1024 threads
+        if (kind == IT_PARTW && threads != 1024) continue;   // wide tiles at 1024 threads only
         KernelFn f = kernel_for(kind, threads);
         if (!f) return (int)cudaErrorInvalidValue;
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);

@@ -33,7 +33,8 @@
 namespace bsx {
 
 enum ItemType : uint32_t { IT_HIST = 0, IT_PART = 1, IT_BUCKET = 2, IT_GSCATTER = 3, IT_GSCAN = 4,
-                           IT_PARTS = 5 /* PART tiles streamed through bulk copies (phase kernel only) */ };
+                           IT_PARTS = 5 /* PART tiles streamed through bulk copies (phase kernel only) */,
+                           IT_PARTW = 6 /* PART with wide tiles, 32 keys a thread (phase kernel, 1024 threads) */ };
 
 enum SyncSlot : uint32_t {
     SY_HIST_DONE = 0,     // HIST tiles finished
@@ -169,6 +170,7 @@ inline uint32_t part_stream_smem_bytes(uint32_t nslices, uint32_t tile_keys) {
 }
 
 constexpr int kKeysPerThread = 16;   // keys per thread in one HIST/PART/GSCATTER tile
+constexpr int kWideKeysPerThread = 32;   // keys per thread in one wide PART tile (IT_PARTW)
 constexpr uint32_t kMaxSlices = 8192;   // bucket ids fit 16 bits in the partition tile
 
 // Host-side launch entry points (engine.cu).

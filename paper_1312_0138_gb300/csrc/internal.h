@@ -26,6 +26,7 @@ struct bsx_config {
     bool summary = true;     // sparse slices keep a summary bitmap (word emission)
     bool stream_part = false; // phased PARTITION: stream tiles through bulk copies when keys are 16-byte aligned
     int part_threads = 0;     // phased PARTITION: block size of the HIST/PART phases (0 = the plan's rule)
+    uint32_t part_tile_keys = 0; // phased PARTITION at 1024 threads: 16384 or 32768 keys a tile (0 = the plan's rule)
     double ms = 0;           // measured time when tuned (0 = not measured)
 };
 
@@ -124,6 +125,7 @@ struct bsx_single_plan {
     bsx::ArrayDesc a;                 // descriptor shape; pointers null
     int Tp = 0, Tb = 0;               // block size of the HIST/PART phases and of the BUCKET phase
     bool stream_part = false;         // the partition streams its tiles through bulk copies
+    bool wide_part = false;           // the partition takes wide tiles (IT_PARTW, 1024 threads)
     uint32_t slice_smem = 0, part_smem = 0, hist_smem = 0;   // dynamic shared memory per phase (bytes)
     uint32_t engine_smem = 0;         // persistent plan: of the one launch
 };

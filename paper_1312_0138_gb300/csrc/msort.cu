@@ -60,7 +60,7 @@ constexpr uint64_t kFlagPrefix = 2ull << 32;   // count of the group up to and i
 constexpr int kEpochShift = 34;
 constexpr uint32_t kEpochMax = (1u << 30) - 1;
 
-constexpr int kKindHist = 6, kKindSplit = 7;   // phase-timing kinds
+constexpr int kKindHist = 16, kKindSplit = 17;   // phase-timing kinds
 
 struct PassArgs {
     const uint32_t *src;

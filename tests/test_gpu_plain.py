@@ -79,6 +79,9 @@ CONFIGS = [
     ("cap_S4096_part512", bs.PATH_PARTITION, 4096, 512, dict(layout=1, part_threads=512)),
     ("exact_S4096_part256", bs.PATH_PARTITION, 4096, 512, dict(layout=0, part_threads=256)),
     ("cap_S64K_part1024_stage", bs.PATH_PARTITION, 1 << 16, 512, dict(layout=1, part_threads=1024, stage=1)),
+    # wide partition tiles (32 Ki keys at 1024 threads): one tile per CTA at these sizes
+    ("cap_S4096_wide", bs.PATH_PARTITION, 4096, 512, dict(layout=1, part_threads=1024, part_tile_keys=32768)),
+    ("exact_odd_wide", bs.PATH_PARTITION, 300_032, 512, dict(layout=0, part_threads=1024, part_tile_keys=32768)),
 ]
 
 
@@ -217,6 +220,34 @@ def test_partition_of_ordered_inputs(ctx, order, S, layout):
         perm = gen.shuffle(62, np.arange(cuts.size, dtype=np.uint32))
         keys = np.concatenate([srt[cuts[i]: cuts[i] + 5000] for i in perm])
     check(ctx, keys, M - 1, path=bs.PATH_PARTITION, S=S, threads=512, layout=layout)
+
+
+# wide partition tiles: 2^26 + k keys make 2049 or more 32 Ki-key tiles, so
+# most CTAs take two or more (each next tile is copied in behind the current
+# one) and the last tile is ragged; keys offset by one element are not
+# 16-byte aligned and every tile is loaded by the threads instead
+WIDE = dict(path=bs.PATH_PARTITION, threads=512, part_threads=1024, part_tile_keys=32768)
+
+
+@pytest.mark.parametrize("S", [1 << 15, 50_048])
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_wide_partition_tiles(ctx, S, layout, offset):
+    n, M = (1 << 26) + 12_345, 1 << 27
+    keys = gen.feistel(gen.SEED_BASE + 71, n, M)
+    check(ctx, keys, M - 1, S=S, layout=layout, offset=offset, **WIDE)
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_wide_partition_range_and_repeats(ctx, layout):
+    n, M = (1 << 26) + 7, 1 << 27
+    keys = gen.feistel(gen.SEED_BASE + 72, n, M)
+    # keys above max_value are skipped and reported
+    check(ctx, keys, M - (1 << 20) - 1, S=1 << 15, layout=layout, **WIDE)
+    # repeated keys: the distinct prefix and DUPLICATE
+    rep = keys.copy()
+    rep[::1000] = rep[1]
+    check(ctx, rep, M - 1, S=1 << 15, layout=layout, **WIDE)
 
 
 @pytest.mark.parametrize("layout", [0, 1])

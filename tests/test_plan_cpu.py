@@ -62,6 +62,7 @@ def test_dense_full_range_capacity_layout():
     assert cfg["path"] == "partition" and cfg["layout"] == "capacity"
     assert sh["scratch_bytes"] == 16 * GIB
     assert cfg["stage"] == 1 and sh["part_threads"] == 1024 and sh["bucket_threads"] == 512
+    assert sh["tile_keys"] == 32768   # wide partition tiles
 
 
 NS = [1, 2, 31, 32, 33, 1000, 4097, 65_536, 65_537, 100_000, 1 << 20, (1 << 20) + 1, 1 << 22, 1 << 24, 1 << 26,
@@ -85,7 +86,11 @@ def test_plan_invariants(sms):
             assert S % 128 == 0 and S >= 128, where
             assert cfg["threads"] in (256, 512, 1024), where
             assert sh["part_threads"] in (256, 512, 1024) and sh["bucket_threads"] in (256, 512, 1024), where
-            assert sh["tile_keys"] == 16 * sh["part_threads"], where
+            # wide partition tiles (32 keys a thread) at 1024 threads where
+            # they fit the shared memory and give every SM eight or more
+            wide = (cfg["path"] == "partition" and sh["part_threads"] == 1024 and -(-n // 32768) >= 8 * sms
+                    and ((sh["slices"] + 4) & ~3) * 16 + 32768 * 4 + 16 <= SMEM)
+            assert sh["tile_keys"] == (32768 if wide else 16 * sh["part_threads"]), where
             if cfg["path"] == "fused":
                 assert M <= 1 << 20 and S >= M and sh["slices"] == 1, where
                 continue
