@@ -338,8 +338,16 @@ extern "C" bitsort_status_t bitsort_server_create(int device, uint64_t budget_by
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     sv->lanes.resize(max_inflight);
-    for (Lane &ln : sv->lanes) {
-        if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
+    // stream 0 (large requests, one after another) at the lowest priority,
+    // the batch streams at the highest: the block scheduler then starts a
+    // batch's CTAs as soon as a large sort's CTAs free an SM, instead of
+    // queueing them behind the large sort's remaining waves
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) prio_low = prio_high = 0;
+    for (size_t li = 0; li < sv->lanes.size(); ++li) {
+        Lane &ln = sv->lanes[li];
+        const int prio = (li == 0 && sv->lanes.size() > 1) ? prio_low : prio_high;
+        if (cudaStreamCreateWithPriority(&ln.stream, cudaStreamNonBlocking, prio) != cudaSuccess ||
             bitsort_ctx_create(device, &ln.ctx) != BITSORT_OK) {
             bitsort_server_destroy(sv);
             return BITSORT_ERR_CUDA;
