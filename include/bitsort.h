@@ -405,13 +405,15 @@ typedef enum {
  *   part_threads    block size of the histogram and partition phases of a
  *                   one-kernel-per-phase plan (256, 512 or 1024); 0 = the
  *                   built-in rule (512 threads, 1024 from 1024 buckets).
- *   part_tile_keys  keys per partition tile when that phase runs at 1024
- *                   threads and its tiles are not streamed: 16384, or 32768
- *                   (wide tiles: a counting sort per tile, with the next
- *                   tile copied in while the current one is written out);
- *                   0 = the built-in rule (32768 when the shared memory
- *                   holds such a tile and there are at least eight tiles
- *                   per SM, else 16384).  Other values count as 0.
+ *   part_tile_keys  keys per partition tile when that phase runs at 512 or
+ *                   1024 threads and its tiles are not streamed: 16 keys a
+ *                   thread (8192 / 16384), or 32 (16384 / 32768: wide tiles,
+ *                   a counting sort per tile, with the next tile copied in
+ *                   while the current one is written out); 0 = the built-in
+ *                   rule (wide when the shared memory holds such a tile and
+ *                   there are at least eight tiles per SM at 1024 threads,
+ *                   four at 512).  A value that matches neither size of the
+ *                   phase's block size counts as 0.
  *   ms              measured time when tuned (output only). */
 typedef struct {
     int32_t path;

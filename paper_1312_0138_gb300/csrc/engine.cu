@@ -1310,8 +1310,9 @@ __device__ void part_stream(const EngineParams &P, const ArrayDesc &a, char *sme
 // Every word read is cleared behind (bitmap and summary), so the slice is zero
 // again for this CTA's next sparse slice without a full clear.
 // ------------------------------------------------- PART with wide tiles
-// The phase kernel's partition at 1024 threads and 32 keys a thread: tiles
-// of 32 Ki keys.  Against part_tile_phase's 16 Ki keys, the per-bucket work
+// The phase kernel's partition at 32 keys a thread: tiles of 32 Ki keys at
+// 1024 threads, 16 Ki at 512.  Against part_tile_phase's 16 keys a thread,
+// the per-bucket work
 // of a tile (reservations, prefixes, run words) is spread over twice the
 // keys, and with thousands of buckets each run the tile leaves in the
 // partition buffer is twice as long (fewer, fuller L2 writes).  Keys and
@@ -1447,7 +1448,7 @@ __device__ __forceinline__ void part_tile_wide(const ArrayDesc &a, uint32_t (&x)
     __syncthreads();
 }
 
-// PART phase with wide tiles (T = 1024, a.tile_keys = 32 * T): a CTA takes
+// PART phase with wide tiles (T = 512 or 1024, a.tile_keys = 32 * T): a CTA takes
 // tiles t, t + G, t + 2G, ...  Shared memory as part_phase.  A tile that is
 // not whole, or keys that are not 16-byte aligned, are loaded by the threads
 // at the start of the tile instead of behind the previous one.  Every copy
@@ -2085,6 +2086,7 @@ static KernelFn kernel_for(int kind, int threads, bool solo = false) {
             case IT_GSCATTER: return phase_kernel<512, IT_GSCATTER>;
             case IT_GSCAN: return phase_kernel<512, IT_GSCAN>;
             case IT_PARTS: return phase_kernel<512, IT_PARTS>;
+            case IT_PARTW: return phase_kernel<512, IT_PARTW>;
         }
     } else if (threads == 1024) {
         // one CTA per SM for the phase kernels of a single sort (the
@@ -2113,7 +2115,7 @@ int engine_set_smem_limit(int threads, uint32_t smem_bytes) {
     for (int kind : {-1, (int)IT_HIST, (int)IT_PART, (int)IT_BUCKET, (int)IT_GSCATTER, (int)IT_GSCAN, (int)IT_PARTS,
                      (int)IT_PARTW}) {
         if (kind == -1 && threads == 1024) continue;   // no persistent engine at 1024 threads
-        if (kind == IT_PARTW && threads != 1024) continue;   // wide tiles at 1024 threads only
+        if (kind == IT_PARTW && threads == 256) continue;   // wide tiles at 512 and 1024 threads
         KernelFn f = kernel_for(kind, threads);
         if (!f) return (int)cudaErrorInvalidValue;
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);

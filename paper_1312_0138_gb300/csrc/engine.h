@@ -34,7 +34,7 @@ namespace bsx {
 
 enum ItemType : uint32_t { IT_HIST = 0, IT_PART = 1, IT_BUCKET = 2, IT_GSCATTER = 3, IT_GSCAN = 4,
                            IT_PARTS = 5 /* PART tiles streamed through bulk copies (phase kernel only) */,
-                           IT_PARTW = 6 /* PART with wide tiles, 32 keys a thread (phase kernel, 1024 threads) */ };
+                           IT_PARTW = 6 /* PART with wide tiles, 32 keys a thread (phase kernel, 512 or 1024 threads) */ };
 
 enum SyncSlot : uint32_t {
     SY_HIST_DONE = 0,     // HIST tiles finished

@@ -82,6 +82,8 @@ CONFIGS = [
     # wide partition tiles (32 Ki keys at 1024 threads): one tile per CTA at these sizes
     ("cap_S4096_wide", bs.PATH_PARTITION, 4096, 512, dict(layout=1, part_threads=1024, part_tile_keys=32768)),
     ("exact_odd_wide", bs.PATH_PARTITION, 300_032, 512, dict(layout=0, part_threads=1024, part_tile_keys=32768)),
+    ("cap_odd_wide512", bs.PATH_PARTITION, 883_072, 512, dict(layout=1, part_threads=512, part_tile_keys=16384)),
+    ("exact_S4096_wide512", bs.PATH_PARTITION, 4096, 512, dict(layout=0, part_threads=512, part_tile_keys=16384)),
 ]
 
 
@@ -227,6 +229,8 @@ def test_partition_of_ordered_inputs(ctx, order, S, layout):
 # one) and the last tile is ragged; keys offset by one element are not
 # 16-byte aligned and every tile is loaded by the threads instead
 WIDE = dict(path=bs.PATH_PARTITION, threads=512, part_threads=1024, part_tile_keys=32768)
+# the same tiles at 512 threads (16 Ki keys, two CTAs per SM)
+WIDE512 = dict(path=bs.PATH_PARTITION, threads=512, part_threads=512, part_tile_keys=16384)
 
 
 @pytest.mark.parametrize("S", [1 << 15, 50_048])
@@ -236,6 +240,21 @@ def test_wide_partition_tiles(ctx, S, layout, offset):
     n, M = (1 << 26) + 12_345, 1 << 27
     keys = gen.feistel(gen.SEED_BASE + 71, n, M)
     check(ctx, keys, M - 1, S=S, layout=layout, offset=offset, **WIDE)
+
+
+@pytest.mark.parametrize("S", [1 << 18, 300_032])
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_wide_partition_tiles_512(ctx, S, layout, offset):
+    # 2^26 + k keys in 16 Ki-key tiles: 4097, so that most CTAs take two
+    n, M = (1 << 26) + 4_321, 1 << 27
+    keys = gen.feistel(gen.SEED_BASE + 73, n, M)
+    check(ctx, keys, M - 1, S=S, layout=layout, offset=offset, **WIDE512)
+    if layout == 1 and offset == 0:   # keys above max_value, and repeats
+        check(ctx, keys, M - (1 << 20) - 1, S=S, layout=layout, **WIDE512)
+        rep = keys.copy()
+        rep[::997] = rep[3]
+        check(ctx, rep, M - 1, S=S, layout=layout, **WIDE512)
 
 
 @pytest.mark.parametrize("layout", [0, 1])

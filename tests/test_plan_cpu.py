@@ -40,7 +40,8 @@ def test_dense_2e24_over_2e28_two_slices_per_sm():
     assert sh["slices"] == 2 * SMS
     assert cfg["slice_values"] == 883_072     # ceil(2^28 / 304) rounded up to 128
     assert cfg["stage"] == 0                   # density 1/16: lanes store their own positions
-    assert sh["part_threads"] == 512 and sh["bucket_threads"] == 512 and sh["tile_keys"] == 8192
+    # wide partition tiles of 16 Ki keys at 512 threads (1024 tiles, four or more per SM)
+    assert sh["part_threads"] == 512 and sh["bucket_threads"] == 512 and sh["tile_keys"] == 16384
     assert sh["scratch_bytes"] == 304 * 883_072 * 4
 
 
@@ -86,11 +87,14 @@ def test_plan_invariants(sms):
             assert S % 128 == 0 and S >= 128, where
             assert cfg["threads"] in (256, 512, 1024), where
             assert sh["part_threads"] in (256, 512, 1024) and sh["bucket_threads"] in (256, 512, 1024), where
-            # wide partition tiles (32 keys a thread) at 1024 threads where
-            # they fit the shared memory and give every SM eight or more
-            wide = (cfg["path"] == "partition" and sh["part_threads"] == 1024 and -(-n // 32768) >= 8 * sms
-                    and ((sh["slices"] + 4) & ~3) * 16 + 32768 * 4 + 16 <= SMEM)
-            assert sh["tile_keys"] == (32768 if wide else 16 * sh["part_threads"]), where
+            # wide partition tiles (32 keys a thread) at 512 or 1024 threads
+            # where they fit the shared memory and give every SM four (512)
+            # or eight (1024) or more
+            pt = sh["part_threads"]
+            wide = (cfg["path"] == "partition" and pt in (512, 1024)
+                    and -(-n // (32 * pt)) >= (8 if pt == 1024 else 4) * sms
+                    and ((sh["slices"] + 4) & ~3) * 16 + 32 * pt * 4 + 16 <= SMEM)
+            assert sh["tile_keys"] == (32 if wide else 16) * pt, where
             if cfg["path"] == "fused":
                 assert M <= 1 << 20 and S >= M and sh["slices"] == 1, where
                 continue
