@@ -411,7 +411,7 @@ typedef enum {
  *                   a counting sort per tile, with the next tile copied in
  *                   while the current one is written out); 0 = the built-in
  *                   rule (wide when the shared memory holds such a tile and
- *                   there are at least eight tiles per SM at 1024 threads,
+ *                   there are at least three tiles per SM at 1024 threads,
  *                   four at 512).  A value that matches neither size of the
  *                   phase's block size counts as 0.
  *   ms              measured time when tuned (output only). */

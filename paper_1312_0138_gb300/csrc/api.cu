@@ -474,26 +474,28 @@ void bsx_plan_single(int sms, uint32_t smem_optin, const bsx_config &cfg0, uint6
         const uint32_t part_smem =
             pl.stream_part ? part_stream_smem_bytes(a.nslices, wide) : part_phase_smem_bytes(a.nslices, wide);
         if (a.nslices >= 1024 && part_smem <= smem_optin) Tp = 1024;
-        if (!cfg.stage && cfg.emit == EMIT_WORD && a.nslices >= 4u * (uint32_t)sms &&
-            slice_smem_bytes(cfg.S, 1024, false) <= smem_optin)
-            Tb = 1024;
     }
+    // the bucket phase's block size, whatever the partition's
+    if (!cfg.persistent && T == 512 && partitioned && !cfg.stage && cfg.emit == EMIT_WORD &&
+        a.nslices >= 4u * (uint32_t)sms && slice_smem_bytes(cfg.S, 1024, false) <= smem_optin)
+        Tb = 1024;
     if (Tp != T) {
         a.tile_keys = (uint32_t)(kKeysPerThread * Tp);
         a.key_tiles = (uint32_t)ceil_div(n, (uint64_t)a.tile_keys);
     }
     // wide partition tiles (32 keys a thread) at 512 or 1024 threads: where
     // the shared memory holds one and the array gives every SM at least
-    // eight of them at 1024 threads (one CTA per SM), four at 512 (two CTAs
+    // three of them at 1024 threads (one CTA per SM), four at 512 (two CTAs
     // per SM); fewer tiles leave SMs idle at the end.  Or where the
     // configuration asks for 32 * Tp keys a tile (16 * Tp keeps them narrow).
     // Measured on GB300: c2a's partition (1024 threads, 4,096 buckets)
-    // 11.82 -> 8.59 ms; c1's (512 threads, 304 buckets) 64.1 -> 62.1 us.
+    // 11.82 -> 8.59 ms; c2b's (1024 threads, 3.4 tiles per SM) 98.6 ->
+    // 84.6 us; c1's (512 threads, 304 buckets) 64.1 -> 62.1 us.
     pl.wide_part = false;
     if (!cfg.persistent && partitioned && !pl.stream_part && (Tp == 1024 || Tp == 512)) {
         const uint32_t wk = (uint32_t)(kWideKeysPerThread * Tp);
         const bool fits = part_phase_smem_bytes(a.nslices, wk) <= smem_optin;
-        const bool many = ceil_div(n, (uint64_t)wk) >= (Tp == 1024 ? 8ull : 4ull) * (uint64_t)sms;
+        const bool many = ceil_div(n, (uint64_t)wk) >= (Tp == 1024 ? 3ull : 4ull) * (uint64_t)sms;
         if (fits && (cfg.part_tile_keys == wk || (cfg.part_tile_keys == 0 && many))) {
             pl.wide_part = true;
             a.tile_keys = wk;

@@ -52,7 +52,7 @@ def test_sparse_full_range_exact_layout_wide_phases():
     cfg, sh = plan(1 << 24, 1 << 32)
     assert cfg["path"] == "partition" and cfg["layout"] == "exact" and sh["scratch_bytes"] == 0
     assert cfg["slice_values"] == 1 << 20 and sh["slices"] == 4096
-    assert sh["part_threads"] == 1024 and sh["tile_keys"] == 16384
+    assert sh["part_threads"] == 1024 and sh["tile_keys"] == 32768   # wide tiles: 512, 3.4 per SM
     assert sh["bucket_threads"] == 1024
 
 
@@ -89,10 +89,10 @@ def test_plan_invariants(sms):
             assert sh["part_threads"] in (256, 512, 1024) and sh["bucket_threads"] in (256, 512, 1024), where
             # wide partition tiles (32 keys a thread) at 512 or 1024 threads
             # where they fit the shared memory and give every SM four (512)
-            # or eight (1024) or more
+            # or three (1024) or more
             pt = sh["part_threads"]
             wide = (cfg["path"] == "partition" and pt in (512, 1024)
-                    and -(-n // (32 * pt)) >= (8 if pt == 1024 else 4) * sms
+                    and -(-n // (32 * pt)) >= (3 if pt == 1024 else 4) * sms
                     and ((sh["slices"] + 4) & ~3) * 16 + 32 * pt * 4 + 16 <= SMEM)
             assert sh["tile_keys"] == (32 if wide else 16) * pt, where
             if cfg["path"] == "fused":
