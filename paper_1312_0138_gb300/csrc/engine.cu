@@ -343,6 +343,13 @@ __device__ __forceinline__ void emit_words(const uint32_t *bm, uint32_t w0, uint
 // modulo 16 bytes; a full buffer leaves as 16-byte vector stores of whole
 // 128-byte lines (a scalar head and tail around them).  Far fewer, fuller L2
 // write requests than storing each step's handful of positions.
+// Index of the highest set bit of x (x != 0).
+__device__ __forceinline__ uint32_t bit_high(uint32_t x) {
+    uint32_t p;
+    asm("bfind.u32 %0, %1;" : "=r"(p) : "r"(x));
+    return p;
+}
+
 __device__ __forceinline__ void stage_flush(const uint32_t *stage, uint32_t s0, uint32_t fill, uint32_t *out,
                                             uint64_t g0, uint64_t lim) {
     const int lane = threadIdx.x & 31;
@@ -390,17 +397,26 @@ __device__ __forceinline__ void emit_words_staged(const uint32_t *bm, uint32_t w
         const uint32_t val = v0 + i * 32u - 1u;
         uint32_t x = v;
         if (s0 + chunk <= cap) {
-            uint32_t *d = stage + s0 + fill + pos;
+            // the highest set bit first, into the word's last slot: one bfind
+            // and one clear per bit, stores at fixed offsets from e, sixteen
+            // slots unrolled (dense words: 16 set bits on average at density
+            // 1/2; c2a's bucket phase 4.44 -> 4.36 ms against the lowest-bit
+            // walk with four unrolled slots)
+            uint32_t *e = stage + s0 + fill + pos + c - 1;
+            const uint32_t vb = val + 1u;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (c > (uint32_t)j) d[j] = val + __ffs(x);
-                x &= x - 1;
+            for (int j = 0; j < 16; ++j) {
+                if (c > (uint32_t)j) {
+                    const uint32_t p = bit_high(x);
+                    e[-j] = vb + p;
+                    x ^= 1u << p;
+                }
             }
-            if (__any_sync(kFull, x != 0)) {
-                d += 4;
-                while (x) {
-                    *d++ = val + __ffs(x);
-                    x &= x - 1;
+            if (__any_sync(kFull, c > 16u)) {
+                for (int j = 16; x; ++j) {
+                    const uint32_t p = bit_high(x);
+                    e[-j] = vb + p;
+                    x ^= 1u << p;
                 }
             }
             fill += chunk;
