@@ -257,6 +257,15 @@ def test_wide_partition_tiles_512(ctx, S, layout, offset):
         check(ctx, rep, M - 1, S=S, layout=layout, **WIDE512)
 
 
+@pytest.mark.parametrize("wide", [WIDE, WIDE512], ids=["1024", "512"])
+def test_wide_partition_in_place(ctx, wide):
+    # keys and output in one buffer: the plan takes the exact layout and the
+    # context's own partition buffer, which the wide tiles fill
+    n, M = (1 << 26) + 999, 1 << 27
+    keys = gen.feistel(gen.SEED_BASE + 74, n, M)
+    check(ctx, keys, M - 1, S=1 << 15, layout=1, inplace=True, **wide)
+
+
 @pytest.mark.parametrize("layout", [0, 1])
 def test_wide_partition_range_and_repeats(ctx, layout):
     n, M = (1 << 26) + 7, 1 << 27
